@@ -1,0 +1,370 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix.
+
+Each ``pin_*`` takes an implementation module (the oracle, or a mutant of it
+with a planted mistake) and raises AssertionError when the fact does not hold.
+No pin retypes the oracle's update formulas: each checks a closed form, an
+invariant, a special case with a derived closed form, or a brute-force
+minimisation of the paper's objective.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+ALBEDO, SPARSE, PENALTY_NO_ALBEDO = 1, 2, 8
+
+
+def tiny_partition(N=40, B=6, seed=0, plume=True, albedo_sigma=0.2):
+    """Small seeded partition drawn from the linearised forward model."""
+    rng = np.random.default_rng(seed)
+    wl = np.linspace(0.0, 1.0, B)
+    mu = 2.0 + 3.0 * np.cos(2.5 * wl) ** 2
+    A = rng.normal(size=(B, B)) * 0.05
+    Cb = A @ A.T + np.diag((mu / 150.0) ** 2)
+    z = rng.multivariate_normal(np.zeros(B), Cb, size=N)
+    a = np.exp(albedo_sigma * rng.normal(size=N))
+    k = -1e-4 * (0.3 + np.exp(-((wl - 0.6) ** 2) / 0.02))
+    alpha = np.zeros(N)
+    if plume:
+        idx = rng.choice(N, size=max(2, N // 8), replace=False)
+        alpha[idx] = rng.uniform(500.0, 4000.0, idx.size)
+    X = a[:, None] * (mu + z) * (1.0 + alpha[:, None] * k[None, :])
+    return X, k, alpha
+
+
+# ---------------------------------------------------------------- P1 Eq. (3)
+def pin_closed_form(impl):
+    """n_iter = 0, no albedo: alpha is the classic matched filter, Eq. (3),
+    with the sample mean and the biased sample covariance (np.cov) and a
+    general LU solve; with albedo each pixel is divided by r_i (Eq. (7))."""
+    for seed in range(3):
+        X, k, _ = tiny_partition(seed=seed)
+        mu = X.mean(axis=0)
+        C = np.cov(X.T, bias=True)
+        t = mu * k
+        v = np.linalg.solve(C, t)
+        mf = (X - mu) @ v / (t @ v)
+        a = impl.retrieve_partition(X, k, lam=0.3, eps=1e-9, n_iter=0, flags=SPARSE)
+        np.testing.assert_allclose(a, mf, rtol=1e-9, atol=1e-9 * np.abs(mf).max())
+        r = X @ mu / (mu @ mu)
+        a = impl.retrieve_partition(X, k, lam=0.3, eps=1e-9, n_iter=0, flags=ALBEDO | SPARSE)
+        np.testing.assert_allclose(a, mf / r, rtol=1e-9, atol=1e-9 * np.abs(mf).max())
+
+
+# ------------------------------------------------- P2 one iteration from zero
+def pin_single_iteration(impl):
+    """alpha_init = 0, one iteration, lam = 0: nothing is removed from the
+    data, so mu^1 = mu^0, C^1 = C^0 and alpha^1 = max(0, Eq. (3))."""
+    X, k, _ = tiny_partition(seed=4)
+    mu = X.mean(axis=0)
+    C = np.cov(X.T, bias=True)
+    t = mu * k
+    v = np.linalg.solve(C, t)
+    mf = (X - mu) @ v / (t @ v)
+    for flags, div in ((0, 1.0), (ALBEDO, X @ mu / (mu @ mu))):
+        a = impl.retrieve_partition(X, k, lam=0.0, eps=1e-9, n_iter=1, flags=flags | SPARSE,
+                                    alpha_init=np.zeros(len(X)))
+        np.testing.assert_allclose(a, np.maximum(mf / div, 0.0), rtol=1e-9,
+                                   atol=1e-9 * np.abs(mf).max())
+        # positivity is applied before the statistics (Sec. III-D): a negative
+        # starting estimate is the same as a zero one
+        a = impl.retrieve_partition(X, k, lam=0.0, eps=1e-9, n_iter=1, flags=flags | SPARSE,
+                                    alpha_init=np.full(len(X), -50.0))
+        np.testing.assert_allclose(a, np.maximum(mf / div, 0.0), rtol=1e-9,
+                                   atol=1e-9 * np.abs(mf).max())
+
+
+# ------------------------------------------------------- P3 non-negativity
+def pin_nonnegative(impl):
+    """Iterative variants never return negative values (Sec. III-D); the
+    non-iterative matched filter does."""
+    X, k, _ = tiny_partition(seed=5, N=60)
+    a0 = impl.retrieve_partition(X, k, lam=1e-3, eps=1e-9, n_iter=0)
+    assert (a0 < 0).any()
+    for n in (1, 2, 5):
+        for flags in (0, ALBEDO, SPARSE, ALBEDO | SPARSE):
+            a = impl.retrieve_partition(X, k, lam=1e-3, eps=1e-9, n_iter=n, flags=flags)
+            assert (a >= 0).all()
+
+
+# ------------------------------------- P4 brute force of the Eq. (8) objective
+def _paper_objective(a_grid, xk, r, C, t, pen):
+    """Eq. (8) for one pixel with the factor-2 reading of the printed step:
+    (x - mu - r a t)^T C^-1 (x - mu - r a t) + 2 pen r a."""
+    # expanded in a: the quadratic's coefficients come from two solves
+    Ci_x = np.linalg.solve(C, xk)
+    Ci_t = np.linalg.solve(C, t)
+    c0, c1, c2 = xk @ Ci_x, t @ Ci_x, t @ Ci_t
+    return c0 - 2.0 * r * a_grid * c1 + (r * a_grid) ** 2 * c2 + 2.0 * pen * r * a_grid
+
+
+def pin_brute_force(impl):
+    """At every iteration each alpha_i^k is the minimiser over a >= 0 of the
+    per-pixel objective built from that iteration's mu^k, C^k, w^k, r_i,
+    found by a dense grid search refined by golden section."""
+    for (B, N, lam, flags) in ((2, 12, 0.0, ALBEDO | SPARSE), (4, 32, 1e-3, ALBEDO | SPARSE),
+                               (8, 32, 1.0, ALBEDO | SPARSE), (4, 32, 1e-3, SPARSE),
+                               (4, 32, 0.5, ALBEDO | SPARSE | PENALTY_NO_ALBEDO)):
+        X, k, _ = tiny_partition(N=N, B=B, seed=10 + B + N)
+        eps = 1e-2
+        alpha, tr = impl.retrieve_partition(X, k, lam=lam, eps=eps, n_iter=3, flags=flags,
+                                            trace=True)
+        r = tr["r"]
+        prev = np.maximum(tr["alpha"][0], 0.0)
+        for it in range(1, 4):
+            mu, C, t = tr["mu"][it], tr["C"][it], tr["t"][it]
+            w = 1.0 / (prev + eps)
+            pen = lam * w / (r if flags & PENALTY_NO_ALBEDO else 1.0)
+            got = tr["alpha"][it]
+            for i in range(N):
+                xk = X[i] - mu
+                hi = 2.0 * np.abs(tr["alpha"][0]).max() + 1.0 + 2.0 * abs(got[i])
+                grid = np.linspace(0.0, hi, 100001)
+                f = _paper_objective(grid, xk, r[i], C, t, pen[i])
+                j = int(np.argmin(f))
+                lo_, hi_ = grid[max(0, j - 1)], grid[min(len(grid) - 1, j + 1)]
+                g = (np.sqrt(5) - 1) / 2
+                for _ in range(80):
+                    c1 = hi_ - g * (hi_ - lo_)
+                    c2 = lo_ + g * (hi_ - lo_)
+                    f1, f2 = _paper_objective(np.array([c1, c2]), xk, r[i], C, t, pen[i])
+                    if f1 < f2:
+                        hi_ = c2
+                    else:
+                        lo_ = c1
+                best = 0.5 * (lo_ + hi_)
+                step = grid[1] - grid[0]
+                assert abs(best - got[i]) <= max(step, 1e-7 * hi), (B, N, lam, it, i, best, got[i])
+            prev = got
+
+
+def pin_kkt(impl):
+    """Optimality of each step: where alpha^k > 0 the derivative of the
+    per-pixel objective vanishes, where alpha^k = 0 it is non-negative."""
+    X, k, _ = tiny_partition(N=80, B=8, seed=21)
+    lam, eps = 1e-3, 1e-6
+    _, tr = impl.retrieve_partition(X, k, lam=lam, eps=eps, n_iter=4, trace=True)
+    r = tr["r"]
+    prev = np.maximum(tr["alpha"][0], 0.0)
+    for it in range(1, 5):
+        mu, C, t, a = tr["mu"][it], tr["C"][it], tr["t"][it], tr["alpha"][it]
+        Ci_t = np.linalg.solve(C, t)
+        pen = lam / (prev + eps)
+        # d/da [(xk - r a t)^T C^-1 (xk - r a t) + 2 pen r a]
+        grad = -2 * r * ((X - mu) @ Ci_t) + 2 * r * r * a * (t @ Ci_t) + 2 * pen * r
+        scale = np.abs(2 * r * ((X - mu) @ Ci_t)).max()
+        pos = a > 0
+        assert np.all(np.abs(grad[pos]) <= 1e-8 * scale)
+        assert np.all(grad[~pos] >= -1e-8 * scale)
+        prev = a
+
+
+# ---------------------------------------------------------------- P6 - P11
+def pin_scale_invariance(impl):
+    """x -> c x leaves alpha unchanged for every lam: p and q scale alike and
+    r is scale-free (Eqs. (3), (7), (9))."""
+    X, k, _ = tiny_partition(N=60, B=8, seed=31)
+    for lam in (0.0, 1e-3):
+        a = impl.retrieve_partition(X, k, lam=lam, eps=1e-9, n_iter=4)
+        b = impl.retrieve_partition(7.3 * X, k, lam=lam, eps=1e-9, n_iter=4)
+        np.testing.assert_allclose(a, b, rtol=1e-7, atol=1e-7 * np.abs(a).max())
+
+
+def pin_band_permutation(impl):
+    """Permuting bands of the data and of s together changes nothing."""
+    X, k, _ = tiny_partition(N=60, B=8, seed=32)
+    perm = np.random.default_rng(0).permutation(8)
+    a = impl.retrieve_partition(X, k, lam=1e-3, eps=1e-9, n_iter=4)
+    b = impl.retrieve_partition(X[:, perm], k[perm], lam=1e-3, eps=1e-9, n_iter=4)
+    np.testing.assert_allclose(a, b, rtol=1e-8, atol=1e-8 * np.abs(a).max())
+
+
+def pin_row_permutation(impl):
+    """Permuting pixels permutes alpha the same way (statistics are sums)."""
+    X, k, _ = tiny_partition(N=60, B=8, seed=33)
+    perm = np.random.default_rng(1).permutation(60)
+    a = impl.retrieve_partition(X, k, lam=1e-3, eps=1e-9, n_iter=4)
+    b = impl.retrieve_partition(X[perm], k, lam=1e-3, eps=1e-9, n_iter=4)
+    np.testing.assert_allclose(a[perm], b, rtol=1e-8, atol=1e-8 * np.abs(a).max())
+
+
+def pin_duplication(impl):
+    """With the 1/N normalisation of Fig. 1, duplicating every pixel leaves
+    mu, C, r and hence alpha unchanged, for every lam.  (A 1/(N-1)
+    normalisation would change C and, through lam w, alpha.)"""
+    X, k, _ = tiny_partition(N=40, B=6, seed=34)
+    for lam in (0.0, 1e-3, 0.3):
+        a = impl.retrieve_partition(X, k, lam=lam, eps=1e-3, n_iter=4)
+        b = impl.retrieve_partition(np.vstack([X, X]), k, lam=lam, eps=1e-3, n_iter=4)
+        np.testing.assert_allclose(b[:40], a, rtol=1e-8, atol=1e-8 * np.abs(a).max())
+        np.testing.assert_allclose(b[40:], a, rtol=1e-8, atol=1e-8 * np.abs(a).max())
+
+
+def pin_lambda_zero_scale(impl):
+    """Table I / caption of Fig. 1: "without sparsity, w = 0".  With lam = 0
+    the sparse variant is exactly the iterative-positive variant."""
+    X, k, _ = tiny_partition(N=50, B=6, seed=35)
+    a = impl.retrieve_partition(X, k, lam=0.0, eps=1e-9, n_iter=5, flags=ALBEDO | SPARSE)
+    b = impl.retrieve_partition(X, k, lam=0.7, eps=1e-9, n_iter=5, flags=ALBEDO)
+    np.testing.assert_allclose(a, b, rtol=0, atol=0)
+
+
+def pin_mask_isolation(impl):
+    """Masked / non-finite pixels do not influence the others (Sec. III-A)."""
+    rng = np.random.default_rng(3)
+    rows, cols, B = 50, 3, 6
+    X, k, _ = tiny_partition(N=rows * cols, B=B, seed=36)
+    cube = X.reshape(rows, cols, B).copy()
+    mask = (rng.uniform(size=(rows, cols)) < 0.2).astype(np.uint8)
+    a, st = impl.retrieve(cube, k, 1e-3, 1e-9, 3, mask=mask)
+    cube2 = cube.copy()
+    mr, mc = np.nonzero(mask)
+    cube2[mr, mc] = rng.normal(size=(mr.size, B)) * 1e3
+    cube2[mr[::3], mc[::3]] = np.nan
+    b, _ = impl.retrieve(cube2, k, 1e-3, 1e-9, 3, mask=mask)
+    np.testing.assert_array_equal(a, b)
+    assert np.all(a[mask.astype(bool)] == 0)
+    cube3 = cube.copy()
+    cube3[mask.astype(bool)] = np.nan
+    c, _ = impl.retrieve(cube3, k, 1e-3, 1e-9, 3, mask=None)  # non-finite = excluded
+    np.testing.assert_array_equal(a, c)
+
+
+def pin_partition_independence(impl):
+    """Each partition (detector column group) is processed independently
+    (Sec. II-E): changing one column changes no other column's alpha."""
+    rows, cols, B = 40, 4, 6
+    X, k, _ = tiny_partition(N=rows * cols, B=B, seed=37)
+    cube = X.reshape(rows, cols, B).copy()
+    a, _ = impl.retrieve(cube, k, 1e-3, 1e-9, 3)
+    cube[:, 2] *= 1.0 + 0.1 * np.random.default_rng(0).normal(size=(rows, B))
+    b, _ = impl.retrieve(cube, k, 1e-3, 1e-9, 3)
+    np.testing.assert_array_equal(a[:, [0, 1, 3]], b[:, [0, 1, 3]])
+    # col_group = 2: partitions {0,1}, {2,3}; a remainder group with cols = 5
+    a2, st = impl.retrieve(np.concatenate([cube, cube[:, :1]], axis=1), k, 1e-3, 1e-9, 2,
+                           col_group=2)
+    assert len(st) == 3
+
+
+# ------------------------------------------------- P13 sticky zeros, P14 B=1
+def pin_sticky_zero(impl):
+    """A pixel at 0 has weight 1/eps; it stays at 0 unless its projection
+    exceeds lam/eps (Eq. (5) and the shrinkage step)."""
+    X, k, _ = tiny_partition(N=60, B=8, seed=38)
+    _, tr = impl.retrieve_partition(X, k, lam=1e-3, eps=1e-9, n_iter=5, trace=True)
+    for it in range(1, 5):
+        zero_before = tr["alpha"][it] == 0
+        small_p = tr["p"][it + 1] < 1e-3 / 1e-9
+        assert np.all(tr["alpha"][it + 1][zero_before & small_p] == 0)
+
+
+def pin_single_band(impl):
+    """B = 1 by hand: C = var(x), t = mu s, so alpha^0 = (x - mu)/(r mu s)
+    with r = x/mu."""
+    x = np.array([3.0, 3.5, 2.5, 4.0, 3.2, 2.8, 3.9, 3.1])
+    s = np.array([-1e-4])
+    mu = x.mean()
+    r = x / mu
+    expect = (x - mu) / (r * mu * s[0])
+    a = impl.retrieve_partition(x[:, None], s, lam=0.0, eps=1e-9, n_iter=0)
+    np.testing.assert_allclose(a, expect, rtol=1e-12)
+    e2 = (x - mu) / (mu * s[0])
+    a = impl.retrieve_partition(x[:, None], s, lam=0.0, eps=1e-9, n_iter=0, flags=0)
+    np.testing.assert_allclose(a, e2, rtol=1e-12)
+
+
+# ------------------------------ special case: s constant, t parallel to mu
+def pin_constant_absorption(impl):
+    """With s = c 1, t(mu) = c mu.  The mean update of Eq. (10) (Fig. 1 form)
+    then keeps every mu^k parallel to mu^0: mu^k = g_k mu^0 with the scalar
+    recursion g_k = 1 - c mean(r_i alpha_i^{k-1}) g_{k-1}, g_0 = 1.  The
+    covariance update then reads C^k = (1/N) sum (x_i - h_i mu^0)(.)^T with
+    h_i = g_k (1 + c r_i alpha_i^{k-1}).  Pins the use of t(mu^{k-1}) in the
+    mean, t(mu^k) in d, and the factor r_i in both."""
+    X, _, _ = tiny_partition(N=60, B=6, seed=39)
+    c = -1e-4
+    s = np.full(6, c)
+    _, tr = impl.retrieve_partition(X, s, lam=1e-3, eps=1e-9, n_iter=4, trace=True)
+    mu0 = X.mean(axis=0)
+    r = X @ mu0 / (mu0 @ mu0)
+    g = 1.0
+    prev = np.maximum(tr["alpha"][0], 0.0)
+    for it in range(1, 5):
+        g = 1.0 - c * np.mean(r * prev) * g
+        np.testing.assert_allclose(tr["mu"][it], g * mu0, rtol=1e-12)
+        h = g * (1.0 + c * r * prev)
+        D = X - h[:, None] * mu0[None, :]
+        np.testing.assert_allclose(tr["C"][it], D.T @ D / len(X), rtol=1e-9,
+                                   atol=1e-12 * np.abs(D.T @ D).max())
+        prev = tr["alpha"][it]
+
+
+def pin_single_band_absorption(impl):
+    """With s = c e_j (absorption in band j only), t(mu) = c mu_j e_j.  Then
+    (i) every mu^k equals mu^0 off band j and obeys the scalar recursion
+    mu^k_j = mu^0_j - c mean(r alpha^{k-1}) mu^{k-1}_j on it;
+    (ii) C^k equals C^0 on the block without band j;
+    (iii) C^k[j, b] = C^0[j, b] - c mu^k_j mean(r_i alpha_i^{k-1} (x_ib - mu^0_b))
+    for b != j, and C^k[j, j] = mean((x_ij - mu^0_j - c mu^k_j r_i alpha_i^{k-1}
+    - (mu^k_j - mu^0_j))^2).
+    Closed forms of the mean and covariance updates (Eqs. (10)-(11), Fig. 1)
+    in a geometry where t is far from parallel to mu."""
+    X, _, _ = tiny_partition(N=70, B=6, seed=40)
+    j, c = 3, -2e-4
+    s = np.zeros(6)
+    s[j] = c
+    _, tr = impl.retrieve_partition(X, s, lam=1e-3, eps=1e-9, n_iter=4, trace=True)
+    N = len(X)
+    mu0 = X.mean(axis=0)
+    Xc = X - mu0
+    C0 = Xc.T @ Xc / N
+    r = X @ mu0 / (mu0 @ mu0)
+    off = [b for b in range(6) if b != j]
+    prev = np.maximum(tr["alpha"][0], 0.0)
+    muj = mu0[j]
+    for it in range(1, 5):
+        beta = r * prev
+        muj = mu0[j] - c * beta.mean() * muj
+        mu = tr["mu"][it]
+        np.testing.assert_allclose(mu[off], mu0[off], rtol=1e-13)
+        np.testing.assert_allclose(mu[j], muj, rtol=1e-13)
+        C = tr["C"][it]
+        np.testing.assert_allclose(C[np.ix_(off, off)], C0[np.ix_(off, off)], rtol=1e-10,
+                                   atol=1e-13 * np.abs(C0).max())
+        row = C0[j, off] - c * muj * (beta @ Xc[:, off]) / N
+        np.testing.assert_allclose(C[j, off], row, rtol=1e-9, atol=1e-12 * np.abs(C0).max())
+        cjj = np.mean((Xc[:, j] - c * muj * beta - (muj - mu0[j])) ** 2)
+        np.testing.assert_allclose(C[j, j], cjj, rtol=1e-10)
+        prev = tr["alpha"][it]
+
+
+# ---------------------------------------------------- P5 plume recovery
+def pin_plume_recovery(impl, scene):
+    """Recovery of a known injected plume (Sec. II-G style validation):
+    regression slope near 1 on strongly enhanced pixels, small error there,
+    background noise below the classic matched filter's, many exact zeros,
+    and the classic filter has negative values while the sparse one has none."""
+    cube = scene.cube.cpu().numpy()
+    k = scene.k
+    a, st = impl.retrieve(cube, k, 1e-3, 1e-9, 10)
+    a0, _ = impl.retrieve(cube, k, 1e-3, 1e-9, 0, flags=0)
+    assert np.all(st == 0)
+    X = cube[:, 0].astype(np.float64)
+    mu = X.mean(0)
+    C = np.cov(X.T, bias=True)
+    t = mu * k
+    smf = 1.0 / np.sqrt(t @ np.linalg.solve(C, t))
+    strong = scene.alpha_true > 5 * smf
+    slope = np.polyfit(scene.alpha_true[strong], a[strong], 1)[0]
+    rmse = np.sqrt(np.mean((a[strong] - scene.alpha_true[strong]) ** 2))
+    bg = scene.alpha_true == 0
+    assert 0.9 <= slope <= 1.15, slope
+    assert rmse < 3 * smf, (rmse, smf)
+    assert a[bg].std() < 0.6 * a0[bg].std()
+    assert (a[bg] == 0).mean() > 0.5
+    assert (a0 < 0).any() and (a >= 0).all()
+
+
+PINS = [pin_closed_form, pin_single_iteration, pin_nonnegative, pin_brute_force, pin_kkt,
+        pin_scale_invariance, pin_band_permutation, pin_row_permutation, pin_duplication,
+        pin_lambda_zero_scale, pin_mask_isolation, pin_partition_independence,
+        pin_sticky_zero, pin_single_band, pin_constant_absorption, pin_single_band_absorption]
