@@ -1,0 +1,150 @@
+/*
+ * mf.h -- C ABI of the GB300-native sparse, albedo-corrected matched filter.
+ *
+ * Method: Foote et al., "Fast and Accurate Retrieval of Methane Concentration
+ * from Imaging Spectrometer Data Using Sparsity Prior", IEEE TGRS 2020
+ * (arXiv 2003.02978).  For each detector partition of a radiance cube the
+ * library runs the procedure of Fig. 1 (Algorithm AlbedoReWeightL1Filter):
+ * background mean and covariance, albedo factor r_i (Eq. (7)), target
+ * t = mu (.) s (Eq. (9)), the matched-filter initial estimate (Eq. (3)
+ * divided by r_i), then N_iter reweighted-l1 iterations: weights
+ * w_i = 1/(alpha_i + eps) (Eq. (5)), mean and covariance re-estimated with the
+ * current enhancement removed (Eqs. (10)-(11)), and the non-negative
+ * shrinkage update of alpha_i (Eq. (6) with the albedo factor of Sec. II-C).
+ *
+ * Conventions shared by every entry point:
+ *  - Cube layout is BIP: cube[(row * cols + col) * bands_total + band], float32,
+ *    C-contiguous.  The band window is [band_lo, band_hi); B = band_hi - band_lo.
+ *  - A partition (Sec. II-E) is a group of col_group adjacent columns; the
+ *    remaining columns form one last smaller group.  P = ceil(cols / col_group).
+ *  - Device pointers are CUDA device (or managed) memory owned by the caller.
+ *    "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Functions return mf_status.  Argument/shape errors are returned
+ *    synchronously and nothing is enqueued.  Per-partition numerical failures
+ *    (covariance not positive definite, N <= B) are recorded on the device and
+ *    read back with mf_plan_status(); such a partition gets alpha = NaN on its
+ *    valid pixels.  Masked or non-finite pixels get alpha = 0 and are excluded
+ *    from every statistic.
+ *  - mf_retrieve allocates nothing and never synchronises; a plan may be used
+ *    by one stream at a time.
+ */
+#ifndef MF_H_
+#define MF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mf_plan_s* mf_plan_t;
+
+typedef enum {
+  MF_OK = 0,
+  MF_ERR_INVALID_ARG = 1,      /* bad pointer, size, window, flag combination */
+  MF_ERR_CUDA = 2,             /* a CUDA runtime call failed (see mf_last_error) */
+  MF_ERR_OOM = 3,              /* workspace allocation failed in mf_plan */
+  MF_ERR_NOT_SPD = 4,          /* per partition: covariance not positive definite */
+  MF_ERR_NONFINITE_INPUT = 5,  /* k, lambda or eps not finite */
+  MF_ERR_TIMEOUT = 6,          /* a bounded device-side wait expired */
+  MF_ERR_INTERNAL = 7,
+  MF_ERR_UNSUPPORTED = 8       /* shape outside what this build supports */
+} mf_status;
+
+enum { MF_BIP = 0 };                       /* layout */
+enum { MF_FP32 = 0, MF_BF16SPLIT = 1 };    /* precision of the covariance accumulation */
+
+/* flags */
+#define MF_ALBEDO            1u  /* albedo factor r_i of Eq. (7); off: r_i = 1 (Fig. 1 caption) */
+#define MF_SPARSE            2u  /* reweighted-l1 weights of Eq. (5); off: w = 0 (Fig. 1 caption) */
+#define MF_LITERAL           4u  /* re-accumulate C^k by a full pass and refactor it every
+                                    iteration, as Fig. 1 prints it; off: exact rank-3 update of
+                                    C^0 (same result up to rounding) */
+#define MF_PENALTY_NO_ALBEDO 8u  /* penalty lambda*w_i/r_i instead of lambda*w_i */
+
+typedef struct {
+  int64_t rows;         /* along-track lines */
+  int64_t cols;         /* cross-track detectors */
+  int64_t bands_total;  /* bands stored per pixel */
+  int32_t band_lo;      /* first band of the window */
+  int32_t band_hi;      /* one past the last band of the window */
+  int32_t col_group;    /* adjacent detectors per partition (>= 1) */
+  int32_t layout;       /* MF_BIP */
+  int32_t precision;    /* MF_FP32 | MF_BF16SPLIT */
+  uint32_t flags;       /* MF_ALBEDO | MF_SPARSE | MF_LITERAL | MF_PENALTY_NO_ALBEDO */
+} mf_desc;
+
+/* Validate the descriptor and allocate every device buffer a retrieval of
+ * this shape needs, once (statistics, Cholesky factors, per-block partial
+ * sums, counters, status).  Supported: 8 <= B <= 128, B % 4 == 0,
+ * band_lo % 4 == 0, bands_total % 4 == 0 (16-byte aligned pixel windows),
+ * rows * col_group > B.  Uses the current CUDA device.  *out is owned by the
+ * caller and released with mf_destroy. */
+mf_status mf_plan(const mf_desc* desc, mf_plan_t* out);
+
+/* Release a plan and its device memory (synchronises the device first). */
+void mf_destroy(mf_plan_t plan);
+
+/* Number of partitions P of the plan. */
+int64_t mf_num_partitions(mf_plan_t plan);
+
+/* One full retrieval, Fig. 1 (Algorithm AlbedoReWeightL1Filter), on every
+ * partition, enqueued on `stream`.
+ *   cube       device, (rows, cols, bands_total) float32 BIP
+ *   k          device, B float32: unit absorption spectrum s of Sec. II-D
+ *   lambda     multiplier on the paper's weight w_i (1 = Fig. 1 verbatim,
+ *              0 = no sparsity); eps the constant of Eq. (5), > 0
+ *   n_iter     reweighting iterations N_iter >= 0; with 0 the initial
+ *              estimate alpha^0 is returned unclamped (Table I, non-iterative rows)
+ *   mask       device (rows, cols) uint8, nonzero = excluded, or NULL
+ *   alpha_init device (rows, cols) float32 replacing alpha^0, or NULL
+ *   alpha_out  device (rows, cols) float32: alpha^{N_iter} in ppm*m
+ *   albedo_out device (rows, cols) float32: r_i (1 when MF_ALBEDO is off;
+ *              0 on masked pixels), or NULL
+ * Allocates nothing, does not synchronise. */
+mf_status mf_retrieve(mf_plan_t plan, const float* cube, const float* k, double lambda,
+                      double eps, int32_t n_iter, const uint8_t* mask,
+                      const float* alpha_init, float* alpha_out, float* albedo_out,
+                      void* stream);
+
+/* mf_retrieve with HOST buffers (pageable or pinned).  Copies the cube, k
+ * and mask to plan-owned device staging (allocated on the first call and
+ * reused), retrieves, copies alpha back and synchronises `stream` before
+ * returning.  Same arguments as mf_retrieve, all host pointers. */
+mf_status mf_retrieve_host(mf_plan_t plan, const float* cube, const float* k, double lambda,
+                           double eps, int32_t n_iter, const uint8_t* mask,
+                           float* alpha_out, void* stream);
+
+/* Background statistics of the last retrieval's initialisation (Fig. 1,
+ * initial mean and covariance): mu0 (P, B) and cov0 (P, B, B), float64
+ * DEVICE buffers written on `stream`. */
+mf_status mf_background(mf_plan_t plan, double* mu0, double* cov0, void* stream);
+
+/* Copy the per-partition status of the last retrieval to `status` (HOST,
+ * P int32, values of mf_status).  Synchronises the plan's last stream.
+ * Returns MF_OK if every partition succeeded, else the first failure. */
+mf_status mf_plan_status(mf_plan_t plan, int32_t* status);
+
+/* Kernel timing for roofline reporting.  While enabled, every kernel the
+ * plan launches is bracketed by two CUDA events on its stream (a few
+ * microseconds of host overhead per launch, none on the device). */
+mf_status mf_profile(mf_plan_t plan, int32_t enable);
+
+/* Read and reset the timings accumulated since the last read: for kind i
+ * (0 = statistics kernel, 1 = pixel kernel), ms[i] is the summed device time
+ * and launches[i] the number of launches; n_kinds entries are written (HOST
+ * arrays).  Synchronises the plan's last stream. */
+mf_status mf_profile_read(mf_plan_t plan, double* ms, int64_t* launches, int32_t n_kinds);
+
+/* Static description of a status code. */
+const char* mf_status_string(mf_status s);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* mf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H_ */

@@ -1,0 +1,179 @@
+"""GB300-native sparse, albedo-corrected matched filter (Foote et al., IEEE TGRS
+2020): Python binding of libmf.so.
+
+Every step of the retrieval runs in the library's CUDA kernels; this module
+only marshals arguments (device pointers of torch tensors, the current CUDA
+stream).  There is no CPU path: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from ._native import MfDesc, MFError, check, lib
+
+ALBEDO = 1
+SPARSE = 2
+LITERAL = 4
+PENALTY_NO_ALBEDO = 8
+FP32 = 0
+BF16SPLIT = 1
+DEFAULT_FLAGS = ALBEDO | SPARSE
+
+# the six variants of Table I: (n_iter > 0, flags)
+TABLE_I = {
+    "reference_rmf": (False, 0),
+    "albedo_only_mf": (False, ALBEDO),
+    "iter_pos_no_albedo": (True, 0),
+    "iter_pos_albedo": (True, ALBEDO),
+    "rwl1mf": (True, SPARSE),
+    "albedo_rwl1mf": (True, ALBEDO | SPARSE),
+}
+
+__all__ = ["Plan", "retrieve", "MFError", "ALBEDO", "SPARSE", "LITERAL", "PENALTY_NO_ALBEDO",
+           "FP32", "BF16SPLIT", "TABLE_I", "library_path"]
+
+
+def library_path() -> str:
+    from ._native import LIB_PATH
+    return LIB_PATH
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass(frozen=True)
+class Shape:
+    rows: int
+    cols: int
+    bands_total: int
+    band_lo: int
+    band_hi: int
+    col_group: int
+    flags: int
+    precision: int
+
+
+class Plan:
+    """A retrieval plan: validated shape plus all device workspace (allocated
+    once, on the current CUDA device).  ``retrieve`` allocates nothing."""
+
+    def __init__(self, rows, cols, bands_total, band_lo=0, band_hi=None, col_group=1,
+                 flags=DEFAULT_FLAGS, precision=FP32):
+        band_hi = bands_total if band_hi is None else band_hi
+        self.shape = Shape(int(rows), int(cols), int(bands_total), int(band_lo), int(band_hi),
+                           int(col_group), int(flags), int(precision))
+        d = MfDesc(rows=rows, cols=cols, bands_total=bands_total, band_lo=band_lo,
+                   band_hi=band_hi, col_group=col_group, layout=0, precision=precision,
+                   flags=flags)
+        h = ctypes.c_void_p()
+        check(lib().mf_plan(ctypes.byref(d), ctypes.byref(h)), "mf_plan")
+        self._h = h
+        self.B = band_hi - band_lo
+        self.P = int(lib().mf_num_partitions(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_cube(self, cube):
+        s = self.shape
+        if not (isinstance(cube, torch.Tensor) and cube.is_cuda and cube.dtype == torch.float32):
+            raise TypeError("cube must be a CUDA float32 tensor")
+        if tuple(cube.shape) != (s.rows, s.cols, s.bands_total) or not cube.is_contiguous():
+            raise ValueError(f"cube must be contiguous {(s.rows, s.cols, s.bands_total)}")
+
+    def retrieve(self, cube, k, lam, eps, n_iter, mask=None, alpha_init=None, out=None,
+                 albedo=None, stream=None):
+        """Enqueue one retrieval on ``stream`` (default: current stream).
+        Returns ``out`` (rows, cols) float32 alpha."""
+        s = self.shape
+        self._check_cube(cube)
+        k = torch.as_tensor(k, dtype=torch.float32, device=cube.device).contiguous()
+        if k.numel() != self.B:
+            raise ValueError(f"k must have {self.B} entries")
+        if mask is not None:
+            if mask.dtype != torch.uint8 or tuple(mask.shape) != (s.rows, s.cols) or \
+                    not mask.is_cuda or not mask.is_contiguous():
+                raise ValueError("mask must be a contiguous CUDA uint8 (rows, cols) tensor")
+        if alpha_init is not None:
+            alpha_init = alpha_init.to(device=cube.device, dtype=torch.float32).contiguous()
+        if out is None:
+            out = torch.empty((s.rows, s.cols), dtype=torch.float32, device=cube.device)
+        check(lib().mf_retrieve(self._h, _ptr(cube), _ptr(k), float(lam), float(eps),
+                                int(n_iter), _ptr(mask), _ptr(alpha_init), _ptr(out),
+                                _ptr(albedo), _stream_handle(stream)), "mf_retrieve")
+        self._k_keepalive = k
+        return out
+
+    def retrieve_host(self, cube, k, lam, eps, n_iter, mask=None, out=None, stream=None):
+        """Host-buffer retrieval (numpy arrays or CPU tensors, pinned or not):
+        copies in, retrieves, copies alpha back, synchronises."""
+        s = self.shape
+        cube = torch.as_tensor(cube)
+        assert cube.dtype == torch.float32 and cube.is_contiguous() and not cube.is_cuda
+        k = torch.as_tensor(np.asarray(k, dtype=np.float32)).contiguous()
+        if mask is not None:
+            mask = torch.as_tensor(mask).to(torch.uint8).contiguous()
+        if out is None:
+            out = torch.empty((s.rows, s.cols), dtype=torch.float32)
+        check(lib().mf_retrieve_host(self._h, _ptr(cube), _ptr(k), float(lam), float(eps),
+                                     int(n_iter), _ptr(mask), _ptr(out), _stream_handle(stream)),
+              "mf_retrieve_host")
+        return out
+
+    def status(self) -> np.ndarray:
+        st = (ctypes.c_int32 * self.P)()
+        lib().mf_plan_status(self._h, st)
+        return np.frombuffer(st, dtype=np.int32).copy()
+
+    def background(self, stream=None):
+        """(mu0 (P, B), cov0 (P, B, B)) float64 CUDA tensors of the last retrieval."""
+        mu = torch.empty((self.P, self.B), dtype=torch.float64, device="cuda")
+        cov = torch.empty((self.P, self.B, self.B), dtype=torch.float64, device="cuda")
+        check(lib().mf_background(self._h, _ptr(mu), _ptr(cov), _stream_handle(stream)),
+              "mf_background")
+        return mu, cov
+
+    def profile(self, enable: bool = True):
+        check(lib().mf_profile(self._h, int(enable)), "mf_profile")
+
+    def profile_read(self):
+        """{'stats': (ms, launches), 'pixel': (ms, launches)} since the last read."""
+        ms = (ctypes.c_double * 2)()
+        n = (ctypes.c_int64 * 2)()
+        check(lib().mf_profile_read(self._h, ms, n, 2), "mf_profile_read")
+        return {"stats": (ms[0], n[0]), "pixel": (ms[1], n[1])}
+
+
+_PLANS: dict = {}
+
+
+def retrieve(cube, k, lam=1e-3, eps=1e-9, n_iter=10, mask=None, alpha_init=None, band_lo=0,
+             band_hi=None, col_group=1, flags=DEFAULT_FLAGS, precision=FP32, albedo=False):
+    """Albedo-corrected reweighted-l1 matched filter on a CUDA cube
+    (rows, cols, bands_total); returns alpha (rows, cols) [and r_i]."""
+    rows, cols, bt = cube.shape
+    key = (rows, cols, bt, band_lo, band_hi, col_group, flags, precision, cube.device.index)
+    plan = _PLANS.get(key)
+    if plan is None:
+        plan = _PLANS[key] = Plan(rows, cols, bt, band_lo, band_hi, col_group, flags, precision)
+    alb = torch.empty((rows, cols), dtype=torch.float32, device=cube.device) if albedo else None
+    a = plan.retrieve(cube, k, lam, eps, n_iter, mask=mask, alpha_init=alpha_init, albedo=alb)
+    return (a, alb) if albedo else a

@@ -1,0 +1,209 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Inputs are seeded synthetic cubes (synth/); the oracle receives exactly the
+float32 values the GPU receives.  Bar: normwise relative alpha error
+e_inf, e_2 <= 1e-4 on valid pixels; masked pixels exactly 0; failed
+partitions NaN with status NOT_SPD, as in the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from parity import TOL_FP32, alpha_errors, f32
+from synth import make_scene, workload_scene
+
+pytestmark = pytest.mark.gpu
+
+ALBEDO, SPARSE, LITERAL, PNA = 1, 2, 4, 8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2003_02978_gb300 import build
+    build.build()
+
+
+def gpu_retrieve(cube_np, k, lam, eps, n_iter, mask=None, flags=ALBEDO | SPARSE, col_group=1,
+                 band_lo=0, band_hi=None, alpha_init=None, albedo=False):
+    import paper_2003_02978_gb300 as mfg
+    rows, cols, bt = cube_np.shape
+    cube = torch.from_numpy(np.ascontiguousarray(cube_np, dtype=np.float32)).cuda()
+    m = None if mask is None else torch.from_numpy(np.ascontiguousarray(mask, np.uint8)).cuda()
+    ai = None if alpha_init is None else torch.from_numpy(
+        np.ascontiguousarray(alpha_init, np.float32)).cuda()
+    plan = mfg.Plan(rows, cols, bt, band_lo, band_hi, col_group, flags)
+    alb = torch.empty((rows, cols), dtype=torch.float32, device="cuda") if albedo else None
+    a = plan.retrieve(cube, np.asarray(k, np.float32), lam, eps, n_iter, mask=m, alpha_init=ai,
+                      albedo=alb)
+    torch.cuda.synchronize()
+    out = a.cpu().numpy(), plan.status()
+    if albedo:
+        out = out + (alb.cpu().numpy(),)
+    plan.close()
+    return out
+
+
+def compare(cube_np, k, lam, eps, n_iter, mask=None, flags=ALBEDO | SPARSE, col_group=1,
+            band_lo=0, band_hi=None, alpha_init=None, tol=TOL_FP32):
+    kk = f32(k)
+    ref, st_ref = oracle.retrieve(cube_np.astype(np.float64), kk, lam, eps, n_iter, mask=mask,
+                                  band_lo=band_lo, band_hi=band_hi, col_group=col_group,
+                                  flags=flags,
+                                  alpha_init=None if alpha_init is None else f32(alpha_init))
+    got, st = gpu_retrieve(cube_np, k, lam, eps, n_iter, mask, flags, col_group, band_lo,
+                           band_hi, alpha_init)
+    np.testing.assert_array_equal(st, st_ref)
+    win = cube_np[:, :, band_lo:band_hi]
+    valid = oracle.valid_pixels(win, mask)
+    parts = oracle.partitions(cube_np.shape[1], col_group)
+    failed = np.zeros_like(valid)
+    for pi, (c0, c1) in enumerate(parts):
+        if st_ref[pi] != 0:
+            failed[:, c0:c1] = True
+    # masked / non-finite pixels: exactly 0; failed partitions: NaN on valid pixels
+    assert np.all(got[~valid] == 0.0)
+    assert np.all(np.isnan(got[valid & failed]))
+    ok = valid & ~failed
+    assert np.all(np.isfinite(got[ok]))
+    e_inf, e_2 = alpha_errors(got, ref, ok)
+    assert e_inf <= tol and e_2 <= tol, (e_inf, e_2, np.abs(ref[ok]).max())
+    if n_iter > 0:
+        assert np.all(got[ok] >= 0.0)
+    return got, ref, e_inf, e_2
+
+
+@pytest.mark.parametrize("n_iter", [0, 1, 2, 10])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_small_workload(n_iter, seed):
+    sc, prm = workload_scene("plain-512x16x72", seed=seed)
+    compare(sc.cube.numpy(), sc.k, prm["lam"], prm["eps"], n_iter)
+
+
+@pytest.mark.parametrize("n_iter", [1, 10])
+def test_literal_schedule(n_iter):
+    sc, prm = workload_scene("plain-512x16x72", seed=3)
+    compare(sc.cube.numpy(), sc.k, prm["lam"], prm["eps"], n_iter, flags=ALBEDO | SPARSE | LITERAL)
+
+
+@pytest.mark.parametrize("variant", ["reference_rmf", "albedo_only_mf", "iter_pos_no_albedo",
+                                     "iter_pos_albedo", "rwl1mf", "albedo_rwl1mf"])
+def test_table_i_variants(variant):
+    from paper_2003_02978_gb300 import TABLE_I
+    iterative, flags = TABLE_I[variant]
+    sc, prm = workload_scene("plain-512x16x72", seed=4)
+    compare(sc.cube.numpy(), sc.k, prm["lam"], prm["eps"], 10 if iterative else 0, flags=flags)
+
+
+@pytest.mark.parametrize("lam", [0.0, 1.0])
+def test_lambda(lam):
+    sc, prm = workload_scene("plain-512x16x72", seed=5)
+    compare(sc.cube.numpy(), sc.k, lam, prm["eps"], 10)
+
+
+def test_penalty_without_albedo():
+    sc, prm = workload_scene("plain-512x16x72", seed=6)
+    compare(sc.cube.numpy(), sc.k, 0.5, prm["eps"], 5, flags=ALBEDO | SPARSE | PNA)
+
+
+@pytest.mark.parametrize("rows,cols,bands,G,mask_frac,lo,hi,bt", [
+    (517, 13, 72, 1, 0.05, 0, None, 72),     # ragged rows (not a multiple of 16/128/512)
+    (1000, 9, 8, 1, 0.0, 0, None, 8),        # B = 8
+    (300, 11, 16, 3, 0.1, 0, None, 16),      # groups of 3, remainder group of 2
+    (700, 10, 80, 5, 0.02, 0, None, 80),     # B = 80, groups of 5
+    (260, 17, 72, 2, 0.0, 0, None, 72),      # odd cols, pairs
+    (400, 8, 72, 1, 0.03, 4, 76, 84),        # band window inside a wider cube
+    (2100, 3, 128, 1, 0.0, 0, None, 128),    # B = 128
+])
+def test_ragged_shapes(rows, cols, bands, G, mask_frac, lo, hi, bt):
+    sc = make_scene(rows, cols, bt, n_plumes=2, plume_sigma=(3.0, 6.0),
+                    plume_peak=(800.0, 3000.0), mask_frac=mask_frac, seed=rows + cols)
+    cube = sc.cube.numpy()
+    k = sc.k[lo:hi if hi else bt]
+    mask = None if sc.mask is None else sc.mask.numpy()
+    compare(cube, k, 1e-3, 1e-9, 6, mask=mask, col_group=G, band_lo=lo, band_hi=hi)
+
+
+def test_mask_nan_and_failed_partitions():
+    sc = make_scene(400, 10, 72, n_plumes=1, mask_frac=0.1, nan_masked=True, seed=11)
+    cube = sc.cube.numpy().copy()
+    mask = sc.mask.numpy().copy()
+    mask[:, 3] = 1                      # column 3 entirely masked: N = 0
+    mask[60:, 7] = 1                    # column 7 keeps 60 <= B pixels
+    cube[5, 1, 10] = np.inf             # a non-finite unmasked pixel is excluded
+    got, ref, _, _ = compare(cube, sc.k, 1e-3, 1e-9, 4, mask=mask)
+    assert got[5, 1] == 0.0
+
+
+def test_alpha_init():
+    sc, prm = workload_scene("plain-512x16x72", seed=7)
+    a0 = np.abs(np.random.default_rng(0).normal(size=(512, 16))).astype(np.float32) * 100
+    compare(sc.cube.numpy(), sc.k, prm["lam"], prm["eps"], 3, alpha_init=a0)
+    compare(sc.cube.numpy(), sc.k, prm["lam"], prm["eps"], 0, alpha_init=a0 - 50)
+
+
+def test_albedo_output():
+    sc, prm = workload_scene("plain-512x16x72", seed=8)
+    cube = sc.cube.numpy()
+    _, _, r = gpu_retrieve(cube, sc.k, prm["lam"], prm["eps"], 2, albedo=True)
+    X = cube[:, 0].astype(np.float64)
+    mu = X.mean(0)
+    np.testing.assert_allclose(r[:, 0], X @ mu / (mu @ mu), rtol=2e-6)
+
+
+def test_deterministic():
+    sc, prm = workload_scene("plain-512x16x72", seed=9)
+    a, _ = gpu_retrieve(sc.cube.numpy(), sc.k, prm["lam"], prm["eps"], 10)
+    b, _ = gpu_retrieve(sc.cube.numpy(), sc.k, prm["lam"], prm["eps"], 10)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_background_statistics():
+    import paper_2003_02978_gb300 as mfg
+    sc, prm = workload_scene("plain-512x16x72", seed=10)
+    cube = sc.cube.numpy()
+    plan = mfg.Plan(512, 16, 72)
+    plan.retrieve(sc.cube.cuda(), sc.k, prm["lam"], prm["eps"], 1)
+    mu, cov = plan.background()
+    mu, cov = mu.cpu().numpy(), cov.cpu().numpy()
+    for c in range(16):
+        X = cube[:, c].astype(np.float64)
+        m = X.mean(0)
+        C = (X - m).T @ (X - m) / len(X)
+        np.testing.assert_allclose(mu[c], m, rtol=1e-7)
+        assert np.linalg.norm(cov[c] - C) / np.linalg.norm(C) < 1e-6
+
+
+def test_host_api_matches_device_api():
+    import paper_2003_02978_gb300 as mfg
+    sc, prm = workload_scene("plain-512x16x72", seed=12)
+    cube = sc.cube.numpy()
+    plan = mfg.Plan(512, 16, 72)
+    a_dev = plan.retrieve(sc.cube.cuda(), sc.k, prm["lam"], prm["eps"], 10).cpu().numpy()
+    a_host = plan.retrieve_host(torch.from_numpy(cube).pin_memory(), sc.k, prm["lam"],
+                                prm["eps"], 10).numpy()
+    np.testing.assert_array_equal(a_dev, a_host)
+
+
+@pytest.mark.parametrize("flags", [ALBEDO | SPARSE, ALBEDO | SPARSE | LITERAL])
+def test_flightline_full_size_sampled_columns(flags):
+    """The 4000 x 598 x 72 flightline workload in the bench's launch
+    configuration; the oracle checks a seeded sample of whole partitions
+    (partitions are independent, Sec. II-E)."""
+    import paper_2003_02978_gb300 as mfg
+    sc, prm = workload_scene("flightline-4000x598x72", seed=0, device="cuda")
+    plan = mfg.Plan(4000, 598, 72, flags=flags)
+    a = plan.retrieve(sc.cube, sc.k, prm["lam"], prm["eps"], prm["n_iter"], mask=sc.mask)
+    torch.cuda.synchronize()
+    assert np.all(plan.status() == 0)
+    got = a.cpu().numpy()
+    cols = np.sort(np.random.default_rng(1).choice(598, size=10, replace=False))
+    cols = np.unique(np.concatenate([cols, [0, 597]]))
+    sub = sc.cube[:, cols, :].cpu().numpy()
+    msk = sc.mask[:, cols].cpu().numpy()
+    ref, st = oracle.retrieve(sub.astype(np.float64), f32(sc.k), prm["lam"], prm["eps"],
+                              prm["n_iter"], mask=msk)
+    valid = oracle.valid_pixels(sub, msk)
+    assert np.all(got[:, cols][~valid] == 0)
+    e_inf, e_2 = alpha_errors(got[:, cols], ref, valid)
+    assert e_inf <= TOL_FP32 and e_2 <= TOL_FP32, (e_inf, e_2)
