@@ -118,7 +118,8 @@ mf_status mf_retrieve_host(mf_plan_t plan, const float* cube, const float* k, do
 
 /* Background statistics of the last retrieval's initialisation (Fig. 1,
  * initial mean and covariance): mu0 (P, B) and cov0 (P, B, B), float64
- * DEVICE buffers written on `stream`. */
+ * DEVICE buffers.  Ordered after the retrieval on `stream`; synchronises it
+ * (diagnostic read-back, not for the hot path). */
 mf_status mf_background(mf_plan_t plan, double* mu0, double* cov0, void* stream);
 
 /* Copy the per-partition status of the last retrieval to `status` (HOST,
@@ -132,7 +133,8 @@ mf_status mf_plan_status(mf_plan_t plan, int32_t* status);
 mf_status mf_profile(mf_plan_t plan, int32_t enable);
 
 /* Read and reset the timings accumulated since the last read: for kind i
- * (0 = statistics kernel, 1 = pixel kernel), ms[i] is the summed device time
+ * (0 = statistics kernel, 1 = pixel kernel, 2 = solve kernels), ms[i] is the
+ * summed device time
  * and launches[i] the number of launches; n_kinds entries are written (HOST
  * arrays).  Synchronises the plan's last stream. */
 mf_status mf_profile_read(mf_plan_t plan, double* ms, int64_t* launches, int32_t n_kinds);

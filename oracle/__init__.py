@@ -6,4 +6,5 @@ and the CPU-baseline leg of ``bench.py``; never by the product path.
 from .mf_oracle import *  # noqa: F401,F403
 from .mf_oracle import (ALBEDO, SPARSE, LITERAL, PENALTY_NO_ALBEDO, NotSPD,  # noqa: F401
                         retrieve, retrieve_partition, partitions, matched_filter,
-                        pixel_energy, near_threshold, valid_pixels)
+                        pixel_energy, near_threshold, valid_pixels,
+                        amplification, retrieve_amplification)

@@ -248,6 +248,59 @@ def retrieve(cube, s, lam=1.0, eps=1e-9, n_iter=10, mask=None, band_lo=0, band_h
     return alpha, status
 
 
+def amplification(X, s, lam=1.0, eps=1e-9, n_iter=10, flags=ALBEDO | SPARSE, alpha_init=None):
+    """Per-pixel growth factor of a perturbation through the reweighting
+    iterations, from the derivative of the shrinkage step with respect to the
+    previous estimate (Eq. (5) inside the step of Fig. 1):
+        kappa_i^k = d alpha_i^k / d alpha_i^{k-1}
+                  = lam w_i^2 / (r_i q^k)     (lam w_i^2 / (r_i^2 q^k) with
+                                               PENALTY_NO_ALBEDO)
+    where alpha_i^k > 0, and 0 where the step clamps.  A perturbation of unit
+    size entering at every step grows to A_i^n with A^0 = 1,
+    A^k = 1 + kappa^k A^{k-1}.  Pixels with a small positive previous
+    estimate have kappa >> 1: any rounding there is magnified, in every
+    precision, by this factor.  Returns A (N,)."""
+    _, tr = retrieve_partition(X, s, lam, eps, n_iter, flags, alpha_init, trace=True)
+    N = X.shape[0]
+    A = np.ones(N)
+    if n_iter == 0 or not (flags & SPARSE):
+        return A
+    r = tr["r"]
+    prev = np.maximum(tr["alpha"][0] if alpha_init is None else np.asarray(alpha_init, float), 0.0)
+    for k in range(1, n_iter + 1):
+        q = tr["q"][k]
+        w = 1.0 / (prev + eps)
+        kap = lam * w * w / np.where(r > 0, r * q, np.inf)
+        if flags & PENALTY_NO_ALBEDO:
+            kap = kap / np.where(r > 0, r, np.inf)
+        kap = np.where(tr["alpha"][k] > 0, kap, 0.0)
+        A = 1.0 + kap * A
+        prev = tr["alpha"][k]
+    return A
+
+
+def retrieve_amplification(cube, s, lam=1.0, eps=1e-9, n_iter=10, mask=None, band_lo=0,
+                           band_hi=None, col_group=1, flags=ALBEDO | SPARSE, alpha_init=None):
+    """``amplification`` for every valid pixel of a cube (1 elsewhere)."""
+    cube = np.asarray(cube)
+    rows, cols, bt = cube.shape
+    band_hi = bt if band_hi is None else band_hi
+    win = cube[:, :, band_lo:band_hi]
+    ok = valid_pixels(win, mask)
+    out = np.ones((rows, cols))
+    for (c0, c1) in partitions(cols, col_group):
+        okp = ok[:, c0:c1]
+        X = win[:, c0:c1][okp].astype(np.float64)
+        a0 = None if alpha_init is None else np.asarray(alpha_init)[:, c0:c1][okp]
+        blk = np.ones(okp.shape)
+        try:
+            blk[okp] = amplification(X, s, lam, eps, n_iter, flags, a0)
+        except NotSPD:
+            pass
+        out[:, c0:c1] = blk
+    return out
+
+
 def near_threshold(X, s, lam=1.0, eps=1e-9, n_iter=10, flags=ALBEDO | SPARSE, alpha_init=None,
                    tol=1e-4):
     """Pixels whose pre-clamp value (p - pen)/(r q) came within ``tol`` (in

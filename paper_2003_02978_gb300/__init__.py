@@ -155,11 +155,11 @@ class Plan:
         check(lib().mf_profile(self._h, int(enable)), "mf_profile")
 
     def profile_read(self):
-        """{'stats': (ms, launches), 'pixel': (ms, launches)} since the last read."""
-        ms = (ctypes.c_double * 2)()
-        n = (ctypes.c_int64 * 2)()
-        check(lib().mf_profile_read(self._h, ms, n, 2), "mf_profile_read")
-        return {"stats": (ms[0], n[0]), "pixel": (ms[1], n[1])}
+        """{'stats'|'pixel'|'solve': (ms, launches)} since the last read."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        check(lib().mf_profile_read(self._h, ms, n, 3), "mf_profile_read")
+        return {"stats": (ms[0], n[0]), "pixel": (ms[1], n[1]), "solve": (ms[2], n[2])}
 
 
 _PLANS: dict = {}

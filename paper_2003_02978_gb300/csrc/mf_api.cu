@@ -1,4 +1,6 @@
 // C ABI of the matched-filter library: plans, workspace and launch sequence.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,8 +52,11 @@ struct mf_plan_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int nj = 0;             // template bucket
-  size_t smem_stats = 0, smem_pixel = 0;
+  size_t smem_stats = 0, smem_pixel = 0, smem_sinit = 0, smem_siter = 0, smem_slit = 0;
   int grid_stats = 0, grid_pixel = 0;
+  // tensor maps of the last cube pointer (re-encoded when it changes)
+  const float* map_cube = nullptr;
+  CUtensorMap map_stats{}, map_pixel{};
   cudaStream_t last_stream = nullptr;
   int device = 0;
   // host-I/O staging (mf_retrieve_host)
@@ -79,10 +84,42 @@ int nj_bucket(int B4) {
   return -1;
 }
 
-cudaError_t set_attrs_dispatch(int nj, size_t s1, size_t s3) {
-  cudaError_t e = mf::stats_set_attributes(nj, s1);
-  if (e != cudaSuccess) return e;
-  return mf::pixel_set_attributes(nj, s3);
+cudaError_t set_attrs(const mf_plan_s* pl) {
+  cudaError_t e = mf::stats_set_attributes(pl->nj, pl->smem_stats);
+  if (e == cudaSuccess) e = mf::pixel_set_attributes(pl->nj, pl->smem_pixel);
+  if (e == cudaSuccess) e = mf::solve_set_attributes(pl->smem_sinit, pl->smem_siter, pl->smem_slit);
+  return e;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+// 3-D view (bands_total, cols, rows) of the cube with a box of
+// (B, box_cols, box_rows) float32 elements; out-of-range boxes are zero filled
+bool encode_cube_map(CUtensorMap* m, const mf::Params& p, const float* cube, int box_cols,
+                     int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)p.bands_total, (cuuint64_t)p.cols, (cuuint64_t)p.rows};
+  const cuuint64_t strides[2] = {(cuuint64_t)p.bands_total * sizeof(float),
+                                 (cuuint64_t)p.bands_total * p.cols * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)p.B, (cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(cube), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 constexpr size_t kMaxMarks = 1 << 14;
@@ -109,14 +146,31 @@ void mark_end(mf_plan_s::Mark* m, cudaStream_t s) {
   if (m) cudaEventRecord(m->stop, s);
 }
 
+enum { KIND_STATS = 0, KIND_PIXEL = 1, KIND_SOLVE = 2, KIND_COUNT = 3 };
+
 void stats_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, cudaStream_t s) {
-  mf_plan_s::Mark* m = mark_begin(pl, 0, s);
-  mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, prm, mode);
+  mf_plan_s::Mark* m = mark_begin(pl, KIND_STATS, s);
+  mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, pl->map_stats, prm, mode);
   mark_end(m, s);
 }
-void pixel_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int tail, cudaStream_t s) {
-  mf_plan_s::Mark* m = mark_begin(pl, 1, s);
-  mf::pixel_launch(pl->nj, pl->grid_pixel, pl->smem_pixel, s, prm, mode, tail);
+void pixel_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int acc, cudaStream_t s) {
+  mf_plan_s::Mark* m = mark_begin(pl, KIND_PIXEL, s);
+  mf::pixel_launch(pl->nj, pl->grid_pixel, pl->smem_pixel, s, pl->map_pixel, prm, mode, acc);
+  mark_end(m, s);
+}
+void solve_init_dispatch(mf_plan_s* pl, const mf::Params& prm, cudaStream_t s) {
+  mf_plan_s::Mark* m = mark_begin(pl, KIND_SOLVE, s);
+  mf::solve_init_launch(pl->smem_sinit, s, prm);
+  mark_end(m, s);
+}
+void solve_iter_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, cudaStream_t s) {
+  mf_plan_s::Mark* m = mark_begin(pl, KIND_SOLVE, s);
+  mf::solve_iter_launch(pl->smem_siter, s, prm, mode);
+  mark_end(m, s);
+}
+void solve_literal_dispatch(mf_plan_s* pl, const mf::Params& prm, cudaStream_t s) {
+  mf_plan_s::Mark* m = mark_begin(pl, KIND_SOLVE, s);
+  mf::solve_literal_launch(pl->smem_slit, s, prm);
   mark_end(m, s);
 }
 
@@ -180,25 +234,30 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
   p.flags = d->flags;
   pl->nj = nj_bucket(p.B4);
 
-  // row blocking: pixel kernel blocks of rb rows; statistics chunks sized so
-  // that the statistics grid has several CTAs per SM
-  const int rb = std::max(16, env_int("MF_RB_ROWS", 512));
-  p.rb_rows = std::min(rb, p.rows);
+  // row blocking: pixel kernel blocks of rb rows (a multiple of the stage
+  // height); statistics chunks sized so that the statistics grid has several
+  // CTAs per SM
+  int rb = std::max(mf::kStageRows, env_int("MF_RB_ROWS", 256));
+  rb = (rb + mf::kStageRows - 1) / mf::kStageRows * mf::kStageRows;
+  p.rb_rows = std::min(rb, (p.rows + mf::kStageRows - 1) / mf::kStageRows * mf::kStageRows);
   p.n_rb = (p.rows + p.rb_rows - 1) / p.rb_rows;
+  p.n_ct = (p.cols + mf::kTileCols - 1) / mf::kTileCols;
   int sc = env_int("MF_SC_ROWS", 0);
   if (sc <= 0) {
     const long target_ctas = 2400;
     long nsc = std::max<long>(1, (target_ctas + p.cols - 1) / p.cols);
     sc = (int)((p.rows + nsc - 1) / nsc);
-    sc = std::max(128, (sc + 127) / 128 * 128);
   }
-  p.sc_rows = std::min(sc, p.rows);
+  sc = std::max(mf::kStatRows, (sc + mf::kStatRows - 1) / mf::kStatRows * mf::kStatRows);
+  p.sc_rows = sc;
   p.n_sc = (p.rows + p.sc_rows - 1) / p.sc_rows;
-  const int ncg = (p.cols + mf::kColGroup - 1) / mf::kColGroup;
-  pl->grid_stats = ncg * p.n_sc * mf::kColGroup;
-  pl->grid_pixel = ncg * p.n_rb * mf::kColGroup;
-  pl->smem_stats = mf::stats_smem_bytes(B, p.BA);
+  pl->grid_stats = p.cols * p.n_sc;
+  pl->grid_pixel = p.n_ct * p.n_rb;
+  pl->smem_stats = mf::stats_smem_bytes(B);
   pl->smem_pixel = mf::pixel_smem_bytes(B);
+  pl->smem_sinit = mf::solve_init_smem_bytes(B, p.BA);
+  pl->smem_siter = mf::solve_iter_smem_bytes(B);
+  pl->smem_slit = mf::solve_literal_smem_bytes(B, p.BA);
 
   // workspace
   const size_t P = (size_t)p.P;
@@ -208,18 +267,19 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
     size_t bytes;
   };
   Piece pieces[] = {
-      {(void**)&p.mu0d, P * B * sizeof(double)},
+      {(void**)&p.pilot, P * B * sizeof(float)},
+      {(void**)&p.mu0, P * B * sizeof(float2)},
       {(void**)&p.mu0f, P * B * sizeof(float)},
       {(void**)&p.vf, P * B * sizeof(float)},
-      {(void**)&p.tprev, P * B * sizeof(double)},
-      {(void**)&p.muk, P * B * sizeof(double)},
+      {(void**)&p.zt, P * B * sizeof(float2)},
+      {(void**)&p.tprev, P * B * sizeof(float2)},
+      {(void**)&p.muk, P * B * sizeof(float2)},
       {(void**)&p.S, P * B * B * sizeof(double)},
-      {(void**)&p.L, P * B * B * sizeof(double)},
-      {(void**)&p.invd, P * B * sizeof(double)},
-      {(void**)&p.scal, P * mf::SC_NSCAL * sizeof(double)},
-      {(void**)&p.k1part, P * p.G * p.n_sc * K1E * sizeof(double)},
+      {(void**)&p.Linv, P * B * B * sizeof(float2)},
+      {(void**)&p.pscal, P * 4 * sizeof(float)},
+      {(void**)&p.dscal, P * 4 * sizeof(double)},
+      {(void**)&p.k1part, P * p.G * p.n_sc * K1E * sizeof(float2)},
       {(void**)&p.k3part, P * p.G * p.n_rb * K3E * sizeof(float)},
-      {(void**)&p.counters, P * sizeof(unsigned)},
       {(void**)&p.status, P * sizeof(int)},
   };
   size_t total = 0;
@@ -240,7 +300,7 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
     off += align_up(pc.bytes, 256);
   }
   e = cudaMemset(pl->ws, 0, total);
-  if (e == cudaSuccess) e = set_attrs_dispatch(pl->nj, pl->smem_stats, pl->smem_pixel);
+  if (e == cudaSuccess) e = set_attrs(pl);
   if (e != cudaSuccess) {
     cudaFree(pl->ws);
     delete pl;
@@ -292,14 +352,27 @@ mf_status mf_retrieve(mf_plan_t pl, const float* cube, const float* k, double la
   p.eps = (float)eps;
   p.n_iter = n_iter;
   const bool literal = (p.flags & MF_LITERAL) != 0;
-  MF_CUDA(cudaMemsetAsync(p.counters, 0, (size_t)p.P * sizeof(unsigned), s));
+  if (cube != pl->map_cube) {
+    if (!encode_cube_map(&pl->map_stats, pl->prm, cube, 1, mf::kStatRows) ||
+        !encode_cube_map(&pl->map_pixel, pl->prm, cube, mf::kTileCols, mf::kStageRows)) {
+      pl->map_cube = nullptr;
+      return fail(MF_ERR_CUDA, "cuTensorMapEncodeTiled failed for the cube");
+    }
+    pl->map_cube = cube;
+  }
   MF_CUDA(cudaMemsetAsync(p.status, 0, (size_t)p.P * sizeof(int), s));
-  const int tail = literal ? mf::TAIL_LITERAL : mf::TAIL_FUSED;
   stats_dispatch(pl, p, mf::STAT_INIT, s);
-  pixel_dispatch(pl, p, mf::PIX_INIT, n_iter > 0 ? tail : mf::TAIL_NONE, s);
+  solve_init_dispatch(pl, p, s);
+  pixel_dispatch(pl, p, mf::PIX_INIT, n_iter > 0, s);
   for (int it = 1; it <= n_iter; ++it) {
-    if (literal) stats_dispatch(pl, p, mf::STAT_LITERAL, s);
-    pixel_dispatch(pl, p, mf::PIX_ITER, it < n_iter ? tail : mf::TAIL_NONE, s);
+    if (literal) {
+      solve_iter_dispatch(pl, p, mf::SOLVE_MEAN_ONLY, s);
+      stats_dispatch(pl, p, mf::STAT_LITERAL, s);
+      solve_literal_dispatch(pl, p, s);
+    } else {
+      solve_iter_dispatch(pl, p, mf::SOLVE_FUSED, s);
+    }
+    pixel_dispatch(pl, p, mf::PIX_ITER, it < n_iter, s);
   }
   MF_CUDA(cudaGetLastError());
   pl->last_stream = s;
@@ -338,8 +411,15 @@ mf_status mf_background(mf_plan_t pl, double* mu0, double* cov0, void* stream) {
   if (!pl || !mu0 || !cov0) return fail(MF_ERR_INVALID_ARG, "null argument");
   const mf::Params& p = pl->prm;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  MF_CUDA(cudaMemcpyAsync(mu0, p.mu0d, (size_t)p.P * p.B * sizeof(double),
-                          cudaMemcpyDeviceToDevice, s));
+  // mu0 is stored as double-float pairs: widen on the host side of the copy
+  const size_t n = (size_t)p.P * p.B;
+  std::vector<float2> tmp(n);
+  MF_CUDA(cudaMemcpyAsync(tmp.data(), p.mu0, n * sizeof(float2), cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> mud(n);
+  for (size_t i = 0; i < n; ++i) mud[i] = (double)tmp[i].x + (double)tmp[i].y;
+  MF_CUDA(cudaMemcpyAsync(mu0, mud.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  MF_CUDA(cudaStreamSynchronize(s));
   MF_CUDA(cudaMemcpyAsync(cov0, p.S, (size_t)p.P * p.B * p.B * sizeof(double),
                           cudaMemcpyDeviceToDevice, s));
   return MF_OK;

@@ -10,102 +10,173 @@
 //   iter:  w_i = 1 / (alpha_i^{k-1} + eps) (Eq. (5)), pen = lambda w_i
 //          alpha_i^k = max(0, (p_i - pen) / (r_i q))   (Eq. (6) with r_i, Fig. 1)
 //   beta_i = r_i alpha_i^k, accumulated as sum beta, sum beta^2,
-//          sum beta (rho - 1) and sum beta e_i (B-vector)
-// with v = (C^k)^{-1} t(mu^k) and q = t^T v prepared by the previous tail.
+//          sum beta (rho_i - 1) and sum beta e_i (a B-vector)
+// with v = (C^k)^{-1} t(mu^k) and q = t^T v prepared by the solve kernel.
 //
-// The last CTA of a partition then prepares the next pass:
-//   mu^{k+1} = mu^0 - mean(beta) t^k                     (Eq. (10), exact)
-//   C^{k+1}  = C^0 - (g t^T + t g^T) + mean(beta)^2 dd^T + var(beta) t t^T
-//              with t = t^{k+1}, d = t^k - t^{k+1}, g = mean(beta (x - mu^0))
-//   which is Eq. (11) expanded exactly: a rank-3 update U M U^T of C^0.
-//   v = (C^{k+1})^{-1} t through C^0's Cholesky factor and the Woodbury
-//   identity: v = z_t - Z (I + M Z^T U ...)^{-1} ..., all in float64.
-// In the literal schedule the tail only forms mu^{k+1} and t^{k+1}; the
-// statistics kernel then re-accumulates and refactorises C^{k+1}.
+// Layout: a CTA owns a tile of 16 adjacent detector columns over a block of
+// rows.  Each pipeline stage is one TMA box of 8 rows x 16 columns x B bands
+// (contiguous 16 x B x 4 bytes per row in HBM), double buffered on
+// mbarriers; warp w consumes row w of a stage, lane pair s column s, so every
+// lane pair keeps the same column (partition) and its moments in registers.
+// alpha and the mask of the next stage are prefetched into registers.
 #include "mf_common.cuh"
 #include "mf_pixel_io.cuh"
+#include "mf_tma.cuh"
 #include "../../include/mf.h"
 
 namespace mf {
 
-size_t pixel_smem_bytes(int B) { return (size_t)(12 * B + 64) * sizeof(double); }
+namespace {
+struct PixSmem {
+  size_t stage_bytes, bar_off, par_off, total;
+};
+__host__ __device__ inline PixSmem pix_layout(int B) {
+  PixSmem L;
+  L.stage_bytes = (size_t)kStageRows * kTileCols * B * sizeof(float);
+  L.bar_off = kPixStages * L.stage_bytes;
+  L.par_off = L.bar_off + 2 * kPixStages * sizeof(uint64_t);
+  // per column: mu0f[B], v[B], 4 scalars
+  L.total = L.par_off + (size_t)kTileCols * (2 * B + 4) * sizeof(float);
+  return L;
+}
+}  // namespace
 
-__device__ void pixel_tail(const Params& p, int tail, int part, int ncp, double* sm,
-                           double* red);
+size_t pixel_smem_bytes(int B) { return pix_layout(B).total + 128; }
 
 template <int NJ>
-__global__ void __launch_bounds__(kThreads) pixel_kernel(Params p, int mode, int tail) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(16) float4 s_mu[kMaxB / 4];
-  __shared__ __align__(16) float4 s_v[kMaxB / 4];
-  __shared__ float s_red[kWarps][kMaxB + 4];
-  __shared__ float s_sc[4];
-  __shared__ int s_last, s_failed;
-  __shared__ double s_dred[kWarps];
+__global__ void __launch_bounds__(kThreads, 2)
+    pixel_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode, int accumulate) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int s_abort;
+  __shared__ int s_failed[kTileCols];
 
-  int c, chunk;
-  unit_of_block(p, p.n_rb, c, chunk);
-  if (c >= p.cols) return;
-  const int part = part_of(p, c);
-  const int c0 = part * p.G;
-  const int ncp = part_ncols(p, part);
+  const int ct = blockIdx.x % p.n_ct;
+  const int rb = blockIdx.x / p.n_ct;
+  const int c0t = ct * kTileCols;
+  const int nc = min(kTileCols, p.cols - c0t);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int B = p.B, B4 = p.B4;
-  const size_t pb = (size_t)part * B;
+  const PixSmem L = pix_layout(B);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bar_off);
+  uint64_t* empty = full + kPixStages;
+  float* s_mu = reinterpret_cast<float*>(smem_raw + L.par_off);
+  float* s_v = s_mu + kTileCols * B;
+  float* s_sc = s_v + kTileCols * B;
 
-  for (int f = tid; f < B4; f += kThreads) {
-    s_mu[f] = reinterpret_cast<const float4*>(p.mu0f + pb)[f];
-    s_v[f] = reinterpret_cast<const float4*>(p.vf + pb)[f];
-  }
+  const int r_beg = rb * p.rb_rows;
+  const int r_end = min(p.rows, r_beg + p.rb_rows);
+  const int nst = (r_end - r_beg + kStageRows - 1) / kStageRows;
+  const uint32_t box_bytes = (uint32_t)(kStageRows * kTileCols * B * sizeof(float));
+
   if (tid == 0) {
-    const double* sc = p.scal + (size_t)part * SC_NSCAL;
-    s_sc[0] = (float)sc[SC_Q];
-    s_sc[1] = (float)sc[SC_MUV];
-    s_sc[2] = (float)sc[SC_COFF];
-    s_sc[3] = (float)sc[SC_INVMU2];
-    s_failed = p.status[part] != MF_OK;
+    s_abort = 0;
+    for (int s = 0; s < kPixStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kWarps);
+    }
+    mbar_fence_init();
   }
   __syncthreads();
-  const float q = s_sc[0], muv = s_sc[1], coff = s_sc[2], invmu2 = s_sc[3];
-  const bool failed = s_failed != 0;
+  int issued[kPixStages] = {0};  // copies issued per stage buffer (thread 0)
+  if (tid == 0) {
+    prefetch_tmap(&map);
+    for (int s = 0; s < kPixStages && s < nst; ++s) {
+      mbar_arrive_expect_tx(&full[s], box_bytes);
+      tma_load_3d(smem_raw + s * L.stage_bytes, &map, p.band_lo, c0t, r_beg + s * kStageRows,
+                  &full[s]);
+      ++issued[s];
+    }
+  }
+  // per-column parameters of the current pass
+  for (int idx = tid; idx < kTileCols * B; idx += kThreads) {
+    const int cc = idx / B, b = idx % B;
+    float m = 0.f, v = 0.f;
+    if (cc < nc) {
+      const size_t pb = (size_t)part_of(p, c0t + cc) * B + b;
+      m = p.mu0f[pb];
+      v = p.vf[pb];
+    }
+    s_mu[idx] = m;
+    s_v[idx] = v;
+  }
+  if (tid < kTileCols) {
+    float4 sc = make_float4(1.f, 0.f, 0.f, 0.f);
+    int failed = 1;
+    if (tid < nc) {
+      const int part = part_of(p, c0t + tid);
+      sc = reinterpret_cast<const float4*>(p.pscal)[part];
+      failed = p.status[part] != MF_OK;
+    }
+    reinterpret_cast<float4*>(s_sc)[tid] = sc;
+    s_failed[tid] = failed;
+  }
+  __syncthreads();
+
+  const int e = lane & 1;
+  const int s_col = lane >> 1;          // column within the tile
+  const bool col_ok = s_col < nc;
+  const int c = c0t + s_col;
+  const float4 sc = reinterpret_cast<const float4*>(s_sc)[s_col];
+  const float q = sc.x, muv = sc.y, coff = sc.z, invmu2 = sc.w;
+  const bool failed = s_failed[s_col] != 0;
+  const float4* mu4 = reinterpret_cast<const float4*>(s_mu + s_col * B);
+  const float4* v4 = reinterpret_cast<const float4*>(s_v + s_col * B);
   const bool albedo = (p.flags & MF_ALBEDO) != 0;
   const bool sparse = (p.flags & MF_SPARSE) != 0;
   const bool pna = (p.flags & MF_PENALTY_NO_ALBEDO) != 0;
-  const bool acc = tail != TAIL_NONE;
   const float lam = p.lambda, eps = p.eps;
+  const bool iter = mode == PIX_ITER;
+  const float* ain = iter ? p.alpha : p.alpha_init;
 
   float g[NJ][4];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) g[j][0] = g[j][1] = g[j][2] = g[j][3] = 0.f;
   float sb = 0.f, sb2 = 0.f, sba = 0.f;
 
-  const int r_beg = chunk * p.rb_rows;
-  const int r_end = min(p.rows, r_beg + p.rb_rows);
-  const int e = lane & 1;
-  const int slot = lane >> 1;
-  for (int r0 = r_beg + warp * 16; r0 < r_end; r0 += kWarps * 16) {
-    const int row = r0 + slot;
-    const bool inb = row < r_end;
+  // prefetch alpha (previous estimate or alpha_init) and the mask of stage 0
+  auto fetch = [&](int i, float& a_out, int& m_out) {
+    const int row = r_beg + i * kStageRows + warp;
+    a_out = 0.f;
+    m_out = 0;
+    if (i < nst && row < r_end && col_ok) {
+      const size_t pix = (size_t)row * p.cols + c;
+      if (ain) a_out = ain[pix];
+      if (p.mask) m_out = p.mask[pix];
+    }
+  };
+  float a_nx;
+  int m_nx;
+  fetch(0, a_nx, m_nx);
+
+  for (int i = 0; i < nst; ++i) {
+    const int sb_ = i % kPixStages;
+    const float a_cur = a_nx;
+    const int m_cur = m_nx;
+    fetch(i + 1, a_nx, m_nx);
+    if (!mbar_wait(&full[sb_], (uint32_t)((i / kPixStages) & 1))) {
+      atomicExch(&s_abort, 1);
+      break;
+    }
+    const int row = r_beg + i * kStageRows + warp;
+    const bool inb = row < r_end && col_ok;
+    const float* px = reinterpret_cast<const float*>(smem_raw + sb_ * L.stage_bytes) +
+                      (size_t)(warp * kTileCols + s_col) * B;
     float4 x[NJ];
-    const bool fin = load_pixel<NJ>(p, row, c, inb, e, x);
-    const size_t pix = (size_t)(inb ? row : 0) * p.cols + c;
-    const bool valid = inb && fin && (!p.mask || p.mask[pix] == 0);
-    const float rho = pair_dot<NJ>(x, s_mu, e, B4) * invmu2;
-    split_residual<NJ>(x, s_mu, rho, e, B4);
-    const float pe = pair_dot<NJ>(x, s_v, e, B4);
+    const bool fin = lds_pixel<NJ>(px, inb, e, B4, x);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[sb_]);
+    const bool valid = inb && fin && m_cur == 0;
+    const float rho = pair_dot<NJ>(x, mu4, e, B4) * invmu2;
+    split_residual<NJ>(x, mu4, rho, e, B4);
+    const float pe = pair_dot<NJ>(x, v4, e, B4);
     const float pp = pe + (rho - 1.f) * muv - coff;
     const float r = albedo ? rho : 1.f;
     float al;
-    if (mode == PIX_INIT) {
-      float a0;
-      if (p.alpha_init)
-        a0 = inb ? p.alpha_init[pix] : 0.f;
-      else
-        a0 = r > 0.f ? pp / (r * q) : 0.f;
+    if (!iter) {
+      const float a0 = p.alpha_init ? a_cur : (r > 0.f ? pp / (r * q) : 0.f);
       al = p.n_iter == 0 ? a0 : fmaxf(a0, 0.f);
     } else {
-      const float ap = inb ? p.alpha[pix] : 0.f;
-      const float w = sparse ? 1.f / (ap + eps) : 0.f;
+      const float w = sparse ? 1.f / (a_cur + eps) : 0.f;
       float pen = lam * w;
       if (pna) pen = r > 0.f ? pen / r : 0.f;
       al = r > 0.f ? fmaxf((pp - pen) / (r * q), 0.f) : 0.f;
@@ -115,15 +186,21 @@ __global__ void __launch_bounds__(kThreads) pixel_kernel(Params p, int mode, int
     else if (failed)
       al = __int_as_float(0x7fc00000);
     if (inb && e == 0) {
+      const size_t pix = (size_t)row * p.cols + c;
       p.alpha[pix] = al;
-      if (mode == PIX_INIT && p.albedo) p.albedo[pix] = valid ? r : 0.f;
+      if (!iter && p.albedo) p.albedo[pix] = valid ? r : 0.f;
     }
-    if (acc) {
-      const float beta = (valid && !failed && r > 0.f) ? r * al : 0.f;
+    if (accumulate) {
+      const bool use = valid && !failed && r > 0.f;
+      const float beta = use ? r * al : 0.f;
+      if (!use) {  // excluded pixels may hold non-finite bands: 0 * NaN is NaN
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       if (e == 0) {
         sb += beta;
         sb2 = fmaf(beta, beta, sb2);
-        sba = fmaf(beta, rho - 1.f, sba);
+        sba = fmaf(beta, use ? rho - 1.f : 0.f, sba);
       }
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
@@ -133,200 +210,58 @@ __global__ void __launch_bounds__(kThreads) pixel_kernel(Params p, int mode, int
         g[j][3] = fmaf(beta, x[j].w, g[j][3]);
       }
     }
-  }
-  if (!acc) return;
-
-  // ---- CTA reduction of the moments (fixed order)
-#pragma unroll
-  for (int j = 0; j < NJ; ++j)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float v = g[j][u];
-#pragma unroll
-      for (int o = 2; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      g[j][u] = v;
-    }
-  sb = warp_sumf(sb);
-  sb2 = warp_sumf(sb2);
-  sba = warp_sumf(sba);
-  if (lane < 2) {
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      const int f = lane + 2 * j;
-      if (f < B4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) s_red[warp][3 + 4 * f + u] = g[j][u];
+    // refill this stage once every warp has read it
+    if (tid == 0 && i + kPixStages < nst) {
+      if (!mbar_wait(&empty[sb_], (uint32_t)((i / kPixStages) & 1))) {
+        atomicExch(&s_abort, 1);
+      } else {
+        mbar_arrive_expect_tx(&full[sb_], box_bytes);
+        tma_load_3d(smem_raw + sb_ * L.stage_bytes, &map, p.band_lo, c0t,
+                    r_beg + (i + kPixStages) * kStageRows, &full[sb_]);
+        ++issued[sb_];
       }
-    }
-    if (lane == 0) {
-      s_red[warp][0] = sb;
-      s_red[warp][1] = sb2;
-      s_red[warp][2] = sba;
     }
   }
   __syncthreads();
+  if (s_abort) {
+    if (tid == 0) {
+      // bounded wait for the last copy issued on each buffer before the CTA exits
+      for (int s = 0; s < kPixStages; ++s)
+        if (issued[s] > 0) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1));
+      for (int cc = 0; cc < nc; ++cc) p.status[part_of(p, c0t + cc)] = MF_ERR_TIMEOUT;
+    }
+    return;
+  }
+  if (!accumulate) return;
+
+  // ---- moments of the tile, per column: sum over the 8 warps (fixed order)
+  const int E3 = B + 3;
+  float* red = reinterpret_cast<float*>(smem_raw);  // [kWarps][kTileCols][E3]
+  float* mine = red + ((size_t)warp * kTileCols + s_col) * E3;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int f = e + 2 * j;
+    if (f < B4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) mine[3 + 4 * f + u] = g[j][u];
+    }
+  }
+  if (e == 0) {
+    mine[0] = sb;
+    mine[1] = sb2;
+    mine[2] = sba;
+  }
+  __syncthreads();
   const int K3E = k3_entries(B);
-  const int unit = (c - c0) * p.n_rb + chunk;
-  float* dst = p.k3part + ((size_t)part * p.G * p.n_rb + unit) * K3E;
-  for (int t = tid; t < B + 3; t += kThreads) {
+  for (int t = tid; t < nc * E3; t += kThreads) {
+    const int cc = t / E3, j = t % E3;
     float s = 0.f;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += s_red[w][t];
-    dst[t] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    const unsigned prev = atomicAdd(&p.counters[part], 1u);
-    s_last = (prev + 1u == (unsigned)(ncp * p.n_rb)) ? 1 : 0;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (!failed) pixel_tail(p, tail, part, ncp, reinterpret_cast<double*>(smem_raw), s_dred);
-  if (tid == 0) p.counters[part] = 0u;
-}
-
-// 3x3 solve with partial pivoting; returns det(A).
-__device__ double solve3(double A[3][3], double b[3], double y[3]) {
-  int perm[3] = {0, 1, 2};
-  double det = 1.0;
-  for (int col = 0; col < 3; ++col) {
-    int piv = col;
-    for (int r = col + 1; r < 3; ++r)
-      if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
-    if (piv != col) {
-      for (int k = 0; k < 3; ++k) {
-        const double t = A[col][k];
-        A[col][k] = A[piv][k];
-        A[piv][k] = t;
-      }
-      const double t = b[col];
-      b[col] = b[piv];
-      b[piv] = t;
-      const int tp = perm[col];
-      perm[col] = perm[piv];
-      perm[piv] = tp;
-      det = -det;
-    }
-    det *= A[col][col];
-    if (A[col][col] == 0.0) return 0.0;
-    for (int r = col + 1; r < 3; ++r) {
-      const double f = A[r][col] / A[col][col];
-      for (int k = col; k < 3; ++k) A[r][k] -= f * A[col][k];
-      b[r] -= f * b[col];
-    }
-  }
-  for (int r = 2; r >= 0; --r) {
-    double s = b[r];
-    for (int k = r + 1; k < 3; ++k) s -= A[r][k] * y[k];
-    y[r] = s / A[r][r];
-  }
-  return det;
-}
-
-__device__ void pixel_tail(const Params& p, int tail, int part, int ncp, double* sm,
-                           double* red) {
-  const int tid = threadIdx.x;
-  const int B = p.B;
-  const size_t pb = (size_t)part * B;
-  const int K3E = k3_entries(B);
-  double* mom = sm;               // B + 4 reduced moments
-  double* U = mom + (B + 4);      // 3 x B: g, t^{k+1}, t^k - t^{k+1}
-  double* Z = U + 3 * B;          // 3 x B: C0^{-1} U
-  double* m0f = Z + 3 * B;        // mu0f
-  double* mk = m0f + B;           // mu^{k+1}
-  double* vv = mk + B;            // v
-  double* dd = vv + B;            // mu^{k+1} - mu0f
-  __shared__ double s_y[3];
-  __shared__ int s_bad;
-
-  const int nunits = ncp * p.n_rb;
-  const float* P0 = p.k3part + (size_t)part * p.G * p.n_rb * K3E;
-  for (int t = tid; t < B + 3; t += kThreads) {
-    double s = 0.0;
-    for (int u = 0; u < nunits; ++u) s += (double)__ldcg(P0 + (size_t)u * K3E + t);
-    mom[t] = s;
-  }
-  __syncthreads();
-  double* scal = p.scal + (size_t)part * SC_NSCAL;
-  const double N = scal[SC_N];
-  const double sb = mom[0], sb2 = mom[1], sba = mom[2];
-  const double bbar = sb / N;
-  const double var = sb2 / N - bbar * bbar;
-  for (int b = tid; b < B; b += kThreads) {
-    const double mu0 = p.mu0d[pb + b];
-    const double mf = (double)p.mu0f[pb + b];
-    const double tk = p.tprev[pb + b];
-    const double muk1 = mu0 - bbar * tk;
-    const double t1 = muk1 * (double)p.k[b];
-    m0f[b] = mf;
-    mk[b] = muk1;
-    dd[b] = muk1 - mf;
-    // g = mean(beta (x - mu0)), x - mu0 = e + (rho - 1) mu0f + (mu0f - mu0)
-    U[b] = (mom[3 + b] + sba * mf + sb * (mf - mu0)) / N;
-    U[B + b] = t1;
-    U[2 * B + b] = tk - t1;
-    Z[b] = U[b];
-    Z[B + b] = t1;
-    Z[2 * B + b] = tk - t1;
-  }
-  __syncthreads();
-  if (tail == TAIL_LITERAL) {
-    for (int b = tid; b < B; b += kThreads) {
-      p.muk[pb + b] = mk[b];
-      p.tprev[pb + b] = U[B + b];
-    }
-    if (tid == 0) scal[SC_BBAR] = bbar;
-    return;
-  }
-  // Z = C0^{-1} U with C0 = L L^T (float64)
-  block_chol_solve(p.L + pb * B, B, B, p.invd + pb, Z, B, 3);
-  double W[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int b2 = 0; b2 < 3; ++b2) W[a][b2] = block_dot(U + a * B, Z + b2 * B, B, red);
-  if (tid == 0) {
-    // C = C0 + U M U^T; v = C^{-1} t = z_t - Z (I + M W)^{-1} M W[:,1]
-    const double M[3][3] = {{0.0, -1.0, 0.0}, {-1.0, var, 0.0}, {0.0, 0.0, bbar * bbar}};
-    double A3[3][3], rhs[3], y[3];
-    for (int i = 0; i < 3; ++i) {
-      rhs[i] = 0.0;
-      for (int j = 0; j < 3; ++j) {
-        double s = (i == j) ? 1.0 : 0.0;
-        for (int k = 0; k < 3; ++k) s += M[i][k] * W[k][j];
-        A3[i][j] = s;
-        rhs[i] += M[i][j] * W[j][1];
-      }
-    }
-    const double det = solve3(A3, rhs, y);
-    s_bad = !(det > 0.0) || !isfinite(det);
-    s_y[0] = y[0];
-    s_y[1] = y[1];
-    s_y[2] = y[2];
-  }
-  __syncthreads();
-  if (s_bad) {
-    if (tid == 0) p.status[part] = MF_ERR_NOT_SPD;
-    return;
-  }
-  const double y0 = s_y[0], y1 = s_y[1], y2 = s_y[2];
-  for (int b = tid; b < B; b += kThreads)
-    vv[b] = Z[B + b] - (Z[b] * y0 + Z[B + b] * y1 + Z[2 * B + b] * y2);
-  __syncthreads();
-  const double qn = block_dot(U + B, vv, B, red);
-  const double muv = block_dot(m0f, vv, B, red);
-  const double coff = block_dot(dd, vv, B, red);
-  for (int b = tid; b < B; b += kThreads) {
-    p.vf[pb + b] = (float)vv[b];
-    p.tprev[pb + b] = U[B + b];
-    p.muk[pb + b] = mk[b];
-  }
-  if (tid == 0) {
-    scal[SC_Q] = qn;
-    scal[SC_MUV] = muv;
-    scal[SC_COFF] = coff;
-    scal[SC_BBAR] = bbar;
-    if (!(qn > 0.0) || !isfinite(qn)) p.status[part] = MF_ERR_NOT_SPD;
+    for (int w = 0; w < kWarps; ++w) s += red[((size_t)w * kTileCols + cc) * E3 + j];
+    const int col = c0t + cc;
+    const int part = part_of(p, col);
+    const int unit = (col - part * p.G) * p.n_rb + rb;
+    p.k3part[((size_t)part * p.G * p.n_rb + unit) * K3E + j] = s;
   }
 }
 
@@ -342,11 +277,11 @@ cudaError_t pixel_set_attributes(int nj, size_t smem) {
   return cudaErrorInvalidValue;
 }
 
-void pixel_launch(int nj, int grid, size_t smem, cudaStream_t s, const Params& p, int mode,
-                  int tail) {
-#define MF_CASE(NJ)                                                   \
-  case NJ:                                                            \
-    pixel_kernel<NJ><<<grid, kThreads, smem, s>>>(p, mode, tail);     \
+void pixel_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
+                  const Params& p, int mode, int accumulate) {
+#define MF_CASE(NJ)                                                        \
+  case NJ:                                                                 \
+    pixel_kernel<NJ><<<grid, kThreads, smem, s>>>(map, p, mode, accumulate); \
     return;
   switch (nj) { MF_NJ_CASES(MF_CASE) }
 #undef MF_CASE

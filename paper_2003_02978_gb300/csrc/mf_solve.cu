@@ -1,0 +1,620 @@
+// Solve kernels: the small dense linear algebra of the background model, one
+// CTA per partition, all in double-float arithmetic (mf_df.cuh).
+//
+// solve_init (after the initial statistics pass; Fig. 1 initialisation):
+//   reduce the per-CTA augmented moments, assemble mu^0 and
+//   C^0 = (1/N) sum (x_i - mu^0)(x_i - mu^0)^T exactly from them, factorise
+//   C^0 = L L^T (Cholesky), form L^{-1} in place, and solve C^0 v = t^0 with
+//   t^0 = mu^0 (.) s (Eq. (9)); q = t^T v is the normaliser of Eq. (3).
+// solve_iter (after each pixel pass; Fig. 1 loop body, Eqs. (10)-(11)):
+//   mu^{k+1} = mu^0 - mean(beta) t^k and, with t = t^{k+1},
+//   d = t^k - t^{k+1} and g = mean(beta (x - mu^0)),
+//   C^{k+1} = C^0 - (g t^T + t g^T) + mean(beta)^2 d d^T + var(beta) t t^T
+//           = C^0 + U M U^T,  U = [g, t, d],
+//   an exact expansion of Eq. (11).  v = (C^{k+1})^{-1} t follows from C^0's
+//   inverse factor by the Woodbury identity:
+//   v = z_t - Z (I + M W)^{-1} M W e_2,  Z = C0^{-1} U,  W = U^T Z,
+//   with C0^{-1} d = C0^{-1} t^k - C0^{-1} t^{k+1} reusing the previous z_t.
+//   det(C^{k+1}) = det(C^0) det(I + M W) > 0 is checked (positive definite).
+// solve_literal (literal schedule, Fig. 1 as printed): assemble C^k from a
+//   fresh statistics pass over d_i, factorise and solve, every iteration.
+#include "mf_common.cuh"
+#include "mf_df.cuh"
+#include "../../include/mf.h"
+
+namespace mf {
+
+namespace {
+
+__device__ __forceinline__ df ldf(const float2* p, size_t i) {
+  const float2 v = p[i];
+  return df{v.x, v.y};
+}
+__device__ __forceinline__ void stf(float2* p, size_t i, df v) { p[i] = make_float2(v.hi, v.lo); }
+
+__device__ __forceinline__ df shfl_xor_df(df v, int o) {
+  return df{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+// CTA-wide double-float sum, fixed order; every thread gets the result
+__device__ df block_sum_df(df v, df* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_xor_df(v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  df s = red[0];
+  for (int i = 1; i < kWarps; ++i) s = df_add(s, red[i]);
+  return s;
+}
+
+// compensated accumulation of products (Dot2 of Ogita, Rump and Oishi, with
+// double-float factors; the lo*lo product is dropped)
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(df x, df y) {
+    const df pr = two_prod(x.hi, y.hi);
+    const float err = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, pr.lo));
+    const df t = two_sum(s, pr.hi);
+    s = t.hi;
+    c = __fadd_rn(c, __fadd_rn(t.lo, err));
+  }
+  __device__ __forceinline__ df result() const { return fast_two_sum(s, c); }
+};
+
+__device__ df block_dot_df(const df* a, const df* b, int n, df* red) {
+  Dot2 d;
+  for (int i = threadIdx.x; i < n; i += kThreads) d.add(a[i], b[i]);
+  return block_sum_df(d.result(), red);
+}
+
+// reduce the per-CTA augmented moments of `part` into the full symmetric
+// BA x BA matrix A (shared memory)
+__device__ void reduce_k1(const Params& p, int part, df* A) {
+  const int BA = p.BA, K1E = k1_entries(BA), nb = BA / 4;
+  const int nunits = part_ncols(p, part) * p.n_sc;
+  const float2* P0 = p.k1part + (size_t)part * p.G * p.n_sc * K1E;
+  for (int q = threadIdx.x; q < K1E; q += kThreads) {
+    df s{0.f, 0.f};
+    for (int u = 0; u < nunits; ++u) s = df_add(s, ldf(P0, (size_t)u * K1E + q));
+    int bi, bj;
+    block_of(q >> 4, nb, bi, bj);
+    const int w = q & 15;
+    const int i = 4 * bi + (w >> 2), j = 4 * bj + (w & 3);
+    A[i * BA + j] = s;
+    A[j * BA + i] = s;
+  }
+  __syncthreads();
+}
+
+// C = (1/N) sum (e + a u1 + b u2 + u3)(...)^T from the augmented moments,
+// written into the lower triangle (diagonal included) of A's leading B x B
+// block; the border rows/columns B.. of A are read, not written.
+__device__ void assemble(const Params& p, df* A, const df* u1, const df* u2, const df* u3, df invN,
+                         double* S_out) {
+  const int B = p.B, BA = p.BA;
+  const df aa = A[B * BA + B], ab = A[B * BA + B + 1], bb = A[(B + 1) * BA + B + 1];
+  const df a1 = A[B * BA + B + 2], b1 = A[(B + 1) * BA + B + 2], n1 = A[(B + 2) * BA + B + 2];
+  const int cnt = B * (B + 1) / 2;
+  for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
+    int i = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+    while (i * (i + 1) / 2 > idx) --i;
+    while ((i + 1) * (i + 2) / 2 <= idx) ++i;
+    const int j = idx - i * (i + 1) / 2;
+    df v = A[i * BA + j];
+    v = df_fma(A[i * BA + B], u1[j], v);
+    v = df_fma(u1[i], A[j * BA + B], v);
+    v = df_fma(A[i * BA + B + 1], u2[j], v);
+    v = df_fma(u2[i], A[j * BA + B + 1], v);
+    v = df_fma(A[i * BA + B + 2], u3[j], v);
+    v = df_fma(u3[i], A[j * BA + B + 2], v);
+    v = df_fma(aa, df_mul(u1[i], u1[j]), v);
+    v = df_fma(ab, df_add(df_mul(u1[i], u2[j]), df_mul(u2[i], u1[j])), v);
+    v = df_fma(bb, df_mul(u2[i], u2[j]), v);
+    v = df_fma(a1, df_add(df_mul(u1[i], u3[j]), df_mul(u3[i], u1[j])), v);
+    v = df_fma(b1, df_add(df_mul(u2[i], u3[j]), df_mul(u3[i], u2[j])), v);
+    v = df_fma(n1, df_mul(u3[i], u3[j]), v);
+    v = df_mul(v, invN);
+    A[i * BA + j] = v;
+    if (S_out) {
+      const double d = df_to_double(v);
+      S_out[(size_t)i * B + j] = d;
+      S_out[(size_t)j * B + i] = d;
+    }
+  }
+  __syncthreads();
+}
+
+// In-place Cholesky of the lower triangle of the leading n x n block (row
+// stride ld): right-looking, one column per step.  invd[j] = 1 / L_jj.
+// Returns false (uniformly) if a pivot is not > 0.
+__device__ bool cholesky_df(df* A, int n, int ld, df* invd, int* flag) {
+  const int tid = threadIdx.x;
+  if (tid == 0) *flag = 0;
+  for (int j = 0; j < n; ++j) {
+    __syncthreads();
+    if (tid == 0) {
+      const df d = A[j * ld + j];
+      if (!(d.hi > 0.f) || !df_isfinite(d)) {
+        *flag = 1;
+      } else {
+        const df r = df_rsqrt(d);
+        A[j * ld + j] = df_mul(d, r);
+        invd[j] = r;
+      }
+    }
+    __syncthreads();
+    if (*flag) return false;
+    const df r = invd[j];
+    for (int i = j + 1 + tid; i < n; i += kThreads) A[i * ld + j] = df_mul(A[i * ld + j], r);
+    __syncthreads();
+    const int m = n - j - 1;
+    const int cnt = m * (m + 1) / 2;
+    for (int idx = tid; idx < cnt; idx += kThreads) {
+      int ii = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+      while (ii * (ii + 1) / 2 > idx) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= idx) ++ii;
+      const int kk = idx - ii * (ii + 1) / 2;
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      A[i * ld + k] = df_sub(A[i * ld + k], df_mul(A[i * ld + j], A[k * ld + j]));
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// X = L^{-1} stored transposed in the strict upper triangle of A
+// (A[j][i] = X[i][j], j < i); X's diagonal is invd.  Right-looking row
+// elimination of L X = I.
+__device__ void tri_inverse_df(df* A, int n, int ld, const df* invd) {
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < n * n; idx += kThreads) {
+    const int j = idx / n, i = idx % n;
+    if (j < i) A[j * ld + i] = df{0.f, 0.f};
+  }
+  __syncthreads();
+  for (int i = 0; i < n; ++i) {
+    for (int j = tid; j < i; j += kThreads) A[j * ld + i] = df_mul(A[j * ld + i], invd[i]);
+    __syncthreads();
+    const int rows = n - i - 1, cols = i + 1;
+    for (int idx = tid; idx < rows * cols; idx += kThreads) {
+      const int r = i + 1 + idx / cols, j = idx % cols;
+      const df xij = (j == i) ? invd[i] : A[j * ld + i];
+      A[j * ld + r] = df_sub(A[j * ld + r], df_mul(A[r * ld + i], xij));
+    }
+    __syncthreads();
+  }
+}
+
+// solve (L L^T) x = b in place (single right-hand side), L lower in A
+__device__ void chol_solve_df(const df* A, int n, int ld, const df* invd, df* x) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < n; ++j) {
+    __syncthreads();
+    if (tid == 0) x[j] = df_mul(x[j], invd[j]);
+    __syncthreads();
+    for (int i = j + 1 + tid; i < n; i += kThreads) x[i] = df_sub(x[i], df_mul(A[i * ld + j], x[j]));
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    __syncthreads();
+    if (tid == 0) x[j] = df_mul(x[j], invd[j]);
+    __syncthreads();
+    for (int i = tid; i < j; i += kThreads) x[i] = df_sub(x[i], df_mul(A[j * ld + i], x[j]));
+  }
+  __syncthreads();
+}
+
+// 3x3 solve with partial pivoting in double-float; returns det
+__device__ df solve3_df(df A[3][3], df b[3], df y[3]) {
+  df det{1.f, 0.f};
+  for (int col = 0; col < 3; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 3; ++r)
+      if (fabsf(A[r][col].hi) > fabsf(A[piv][col].hi)) piv = r;
+    if (piv != col) {
+      for (int k = 0; k < 3; ++k) {
+        const df t = A[col][k];
+        A[col][k] = A[piv][k];
+        A[piv][k] = t;
+      }
+      const df t = b[col];
+      b[col] = b[piv];
+      b[piv] = t;
+      det = df_neg(det);
+    }
+    det = df_mul(det, A[col][col]);
+    if (A[col][col].hi == 0.f) return df{0.f, 0.f};
+    const df inv = df_recip(A[col][col]);
+    for (int r = col + 1; r < 3; ++r) {
+      const df f = df_mul(A[r][col], inv);
+      for (int k = col; k < 3; ++k) A[r][k] = df_sub(A[r][k], df_mul(f, A[col][k]));
+      b[r] = df_sub(b[r], df_mul(f, b[col]));
+    }
+  }
+  for (int r = 2; r >= 0; --r) {
+    df s = b[r];
+    for (int k = r + 1; k < 3; ++k) s = df_sub(s, df_mul(A[r][k], y[k]));
+    y[r] = df_div(s, A[r][r]);
+  }
+  return det;
+}
+
+__device__ void fail_partition(const Params& p, int part, bool init) {
+  const int B = p.B;
+  const size_t pb = (size_t)part * B;
+  for (int b = threadIdx.x; b < B; b += kThreads) {
+    p.vf[pb + b] = 0.f;
+    if (init) {
+      p.mu0f[pb + b] = 0.f;
+      stf(p.mu0, pb + b, df{0.f, 0.f});
+      stf(p.tprev, pb + b, df{0.f, 0.f});
+      stf(p.zt, pb + b, df{0.f, 0.f});
+    }
+  }
+  if (threadIdx.x == 0) {
+    p.status[part] = MF_ERR_NOT_SPD;
+    reinterpret_cast<float4*>(p.pscal)[part] = make_float4(1.f, 0.f, 0.f, 0.f);
+  }
+}
+
+}  // namespace
+
+size_t solve_init_smem_bytes(int B, int BA) {
+  return ((size_t)BA * BA + 10 * (size_t)B) * sizeof(df) + 64;
+}
+size_t solve_iter_smem_bytes(int B) {
+  return ((size_t)B * B + 12 * (size_t)B + 8) * sizeof(df) + 64;
+}
+size_t solve_literal_smem_bytes(int B, int BA) {
+  return ((size_t)BA * BA + 10 * (size_t)B) * sizeof(df) + 64;
+}
+
+__global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ df red[kWarps];
+  __shared__ int s_flag;
+  const int part = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int B = p.B, BA = p.BA;
+  const size_t pb = (size_t)part * B;
+  df* A = reinterpret_cast<df*>(smem_raw);
+  df* vm = A + (size_t)BA * BA;  // pilot m
+  df* vmu = vm + B;              // mu^0
+  df* vu3 = vmu + B;             // m - mu^0, later mu^0 - mu0f
+  df* vz0 = vu3 + B;             // zeros (no b-coefficient at initialisation)
+  df* vt = vz0 + B;              // t^0
+  df* vy = vt + B;
+  df* vz = vy + B;
+  df* invd = vz + B;
+  df* vmf = invd + B;            // mu0f
+  if (p.status[part] != MF_OK) return;  // the statistics pass timed out
+
+  reduce_k1(p, part, A);
+  const df N = A[(B + 2) * BA + B + 2];
+  const bool enough = N.hi > (float)B;
+  const df invN = enough ? df_recip(N) : df{0.f, 0.f};
+  const df sa = A[B * BA + B + 2];
+  for (int b = tid; b < B; b += kThreads) {
+    const float m = p.pilot[pb + b];
+    vm[b] = df{m, 0.f};
+    // mu^0 = m + (sum e + (sum a) m) / N
+    const df mu = df_add(df{m, 0.f}, df_mul(df_fma(sa, df{m, 0.f}, A[b * BA + B + 2]), invN));
+    vmu[b] = mu;
+    vu3[b] = df_sub(df{m, 0.f}, mu);
+    vz0[b] = df{0.f, 0.f};
+  }
+  __syncthreads();
+  assemble(p, A, vm, vz0, vu3, invN, p.S + (size_t)part * B * B);
+  const bool ok = enough && cholesky_df(A, B, BA, invd, &s_flag);
+  if (!ok) {
+    fail_partition(p, part, true);
+    return;
+  }
+  tri_inverse_df(A, B, BA, invd);
+  for (int b = tid; b < B; b += kThreads) {
+    vt[b] = df_mulf(vmu[b], p.k[b]);
+    const float mf = df_to_float(vmu[b]);
+    vmf[b] = df{mf, 0.f};
+    vu3[b] = df_sub(vmu[b], vmf[b]);
+  }
+  __syncthreads();
+  // y = L^{-1} t
+  for (int i = tid; i < B; i += kThreads) {
+    Dot2 d;
+    d.add(invd[i], vt[i]);
+    for (int j = 0; j < i; ++j) d.add(A[j * BA + i], vt[j]);
+    vy[i] = d.result();
+  }
+  __syncthreads();
+  // z = L^{-T} y
+  for (int j = tid; j < B; j += kThreads) {
+    Dot2 d;
+    d.add(invd[j], vy[j]);
+    for (int i = j + 1; i < B; ++i) d.add(A[j * BA + i], vy[i]);
+    vz[j] = d.result();
+  }
+  __syncthreads();
+  const df q = block_dot_df(vt, vz, B, red);
+  const df muv = block_dot_df(vmf, vz, B, red);
+  const df coff = block_dot_df(vu3, vz, B, red);
+  const df n2 = block_dot_df(vmf, vmf, B, red);
+  // store L^{-1} (row-major, lower with diagonal), mean, target, solution
+  float2* X = p.Linv + (size_t)part * B * B;
+  for (int idx = tid; idx < B * B; idx += kThreads) {
+    const int i = idx / B, j = idx % B;
+    const df v = (j < i) ? A[j * BA + i] : (j == i ? invd[i] : df{0.f, 0.f});
+    stf(X, idx, v);
+  }
+  for (int b = tid; b < B; b += kThreads) {
+    stf(p.mu0, pb + b, vmu[b]);
+    p.mu0f[pb + b] = vmf[b].hi;
+    p.vf[pb + b] = df_to_float(vz[b]);
+    stf(p.zt, pb + b, vz[b]);
+    stf(p.tprev, pb + b, vt[b]);
+    stf(p.muk, pb + b, vmu[b]);
+  }
+  if (tid == 0) {
+    const bool good = q.hi > 0.f && df_isfinite(q);
+    reinterpret_cast<float4*>(p.pscal)[part] =
+        make_float4(df_to_float(q), df_to_float(muv), df_to_float(coff),
+                    1.0f / df_to_float(n2));
+    double* ds = p.dscal + (size_t)part * 4;
+    ds[DS_N] = df_to_double(N);
+    ds[DS_BBAR] = 0.0;
+    ds[DS_Q] = df_to_double(q);
+    ds[DS_N2] = df_to_double(n2);
+    p.status[part] = good ? MF_OK : MF_ERR_NOT_SPD;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ df red[kWarps];
+  __shared__ df s_y[3];
+  __shared__ int s_bad;
+  const int part = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int B = p.B;
+  const size_t pb = (size_t)part * B;
+  if (p.status[part] != MF_OK) return;
+  df* X = reinterpret_cast<df*>(smem_raw);  // L^{-1}, B x B
+  df* mom = X + (size_t)B * B;              // B + 3 moments (padded to B + 8)
+  df* U0 = mom + B + 8;                     // g
+  df* U1 = U0 + B;                          // t^{k+1}
+  df* U2 = U1 + B;                          // t^k - t^{k+1}
+  df* Y0 = U2 + B;
+  df* Y1 = Y0 + B;
+  df* Z0 = Y1 + B;
+  df* Z1 = Z0 + B;
+  df* Z2 = Z1 + B;
+  df* vmf = Z2 + B;
+  df* vmk = vmf + B;
+  df* vv = vmk + B;
+
+  const int K3E = k3_entries(B);
+  const int nunits = part_ncols(p, part) * p.n_rb;
+  const float* P0 = p.k3part + (size_t)part * p.G * p.n_rb * K3E;
+  for (int t = tid; t < B + 3; t += kThreads) {
+    df s{0.f, 0.f};
+    for (int u = 0; u < nunits; ++u) s = df_addf(s, P0[(size_t)u * K3E + t]);
+    mom[t] = s;
+  }
+  __syncthreads();
+  const double* ds = p.dscal + (size_t)part * 4;
+  const df N = df_from_double(ds[DS_N]);
+  const df invN = df_recip(N);
+  const df sb = mom[0], sb2 = mom[1], sba = mom[2];
+  const df bbar = df_mul(sb, invN);
+  const df var = df_sub(df_mul(sb2, invN), df_mul(bbar, bbar));
+  for (int b = tid; b < B; b += kThreads) {
+    const df mu0 = ldf(p.mu0, pb + b);
+    const df mf{p.mu0f[pb + b], 0.f};
+    const df tk = ldf(p.tprev, pb + b);
+    const df mk = df_sub(mu0, df_mul(bbar, tk));
+    const df t1 = df_mulf(mk, p.k[b]);
+    // g = mean(beta (x - mu0)), x - mu0 = e + (rho - 1) mu0f + (mu0f - mu0)
+    df g = df_fma(sba, mf, mom[3 + b]);
+    g = df_fma(sb, df_sub(mf, mu0), g);
+    U0[b] = df_mul(g, invN);
+    U1[b] = t1;
+    U2[b] = df_sub(tk, t1);
+    vmf[b] = mf;
+    vmk[b] = mk;
+  }
+  if (mode == SOLVE_MEAN_ONLY) {
+    __syncthreads();
+    for (int b = tid; b < B; b += kThreads) {
+      stf(p.muk, pb + b, vmk[b]);
+      stf(p.tprev, pb + b, U1[b]);
+    }
+    if (tid == 0) p.dscal[(size_t)part * 4 + DS_BBAR] = df_to_double(bbar);
+    return;
+  }
+  const float2* Xg = p.Linv + (size_t)part * B * B;
+  for (int idx = tid; idx < B * B; idx += kThreads) X[idx] = ldf(Xg, idx);
+  __syncthreads();
+  // Y = L^{-1} [g, t]
+  for (int w = tid; w < 2 * B; w += kThreads) {
+    const int r = w / B, i = w % B;
+    const df* u = r ? U1 : U0;
+    Dot2 d;
+    for (int j = 0; j <= i; ++j) d.add(X[i * B + j], u[j]);
+    (r ? Y1 : Y0)[i] = d.result();
+  }
+  __syncthreads();
+  // Z = L^{-T} Y
+  for (int w = tid; w < 2 * B; w += kThreads) {
+    const int r = w / B, j = w % B;
+    const df* y = r ? Y1 : Y0;
+    Dot2 d;
+    for (int i = j; i < B; ++i) d.add(X[i * B + j], y[i]);
+    (r ? Z1 : Z0)[j] = d.result();
+  }
+  __syncthreads();
+  // C0^{-1} (t^k - t^{k+1}) = z(t^k) - z(t^{k+1})
+  for (int b = tid; b < B; b += kThreads) Z2[b] = df_sub(ldf(p.zt, pb + b), Z1[b]);
+  __syncthreads();
+  const df* Uc[3] = {U0, U1, U2};
+  const df* Zc[3] = {Z0, Z1, Z2};
+  df W[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) W[a][c] = block_dot_df(Uc[a], Zc[c], B, red);
+  if (tid == 0) {
+    // C = C0 + U M U^T;  v = z_t - Z (I + M W)^{-1} M W[:, 1]
+    const df zero{0.f, 0.f}, one{1.f, 0.f}, mone{-1.f, 0.f};
+    const df M[3][3] = {{zero, mone, zero}, {mone, var, zero}, {zero, zero, df_mul(bbar, bbar)}};
+    df A3[3][3], rhs[3], y[3];
+    for (int i = 0; i < 3; ++i) {
+      rhs[i] = zero;
+      for (int j = 0; j < 3; ++j) {
+        df s = (i == j) ? one : zero;
+        for (int k = 0; k < 3; ++k) s = df_fma(M[i][k], W[k][j], s);
+        A3[i][j] = s;
+        rhs[i] = df_fma(M[i][j], W[j][1], rhs[i]);
+      }
+    }
+    // Hadamard ratio |det| / prod ||row||: near 0 when I + M W is close to
+    // singular, i.e. C^{k+1} is far more singular than C^0 along U; the
+    // Woodbury form then loses the digits that a direct factorisation keeps
+    float hr = 1.f;
+    for (int i = 0; i < 3; ++i) {
+      float n2 = 0.f;
+      for (int j = 0; j < 3; ++j) n2 = fmaf(A3[i][j].hi, A3[i][j].hi, n2);
+      hr *= sqrtf(n2);
+    }
+    const df det = solve3_df(A3, rhs, y);
+    hr = fabsf(det.hi) / fmaxf(hr, 1e-30f);
+    s_bad = !(det.hi > 0.f) || !df_isfinite(det) ? 1 : (hr < 1e-8f ? 2 : 0);
+    s_y[0] = y[0];
+    s_y[1] = y[1];
+    s_y[2] = y[2];
+  }
+  __syncthreads();
+  if (s_bad == 1) {
+    fail_partition(p, part, false);
+    return;
+  }
+  if (s_bad == 2) {
+    // direct path: C^{k+1} = C^0 + U M U^T assembled in double-float (into
+    // the L^{-1} buffer, no longer needed), factorised and solved
+    const double* Sg = p.S + (size_t)part * B * B;
+    const df mvar = var, mb2 = df_mul(bbar, bbar);
+    for (int idx = tid; idx < B * B; idx += kThreads) {
+      const int i = idx / B, j = idx % B;
+      if (j > i) continue;
+      df c = df_from_double(Sg[idx]);
+      c = df_sub(c, df_add(df_mul(U0[i], U1[j]), df_mul(U1[i], U0[j])));
+      c = df_fma(mvar, df_mul(U1[i], U1[j]), c);
+      c = df_fma(mb2, df_mul(U2[i], U2[j]), c);
+      X[idx] = c;
+    }
+    for (int b = tid; b < B; b += kThreads) vv[b] = U1[b];
+    __shared__ int s_flag;
+    if (!cholesky_df(X, B, B, Y0, &s_flag)) {  // Y0 holds 1/diag(L)
+      fail_partition(p, part, false);
+      return;
+    }
+    chol_solve_df(X, B, B, Y0, vv);
+  } else {
+    const df y0 = s_y[0], y1 = s_y[1], y2 = s_y[2];
+    for (int b = tid; b < B; b += kThreads) {
+      df zy = df_mul(Z0[b], y0);
+      zy = df_fma(Z1[b], y1, zy);
+      zy = df_fma(Z2[b], y2, zy);
+      vv[b] = df_sub(Z1[b], zy);
+    }
+  }
+  for (int b = tid; b < B; b += kThreads) U2[b] = df_sub(vmk[b], vmf[b]);  // mu^{k+1} - mu0f
+  __syncthreads();
+  const df q = block_dot_df(U1, vv, B, red);
+  const df muv = block_dot_df(vmf, vv, B, red);
+  const df coff = block_dot_df(U2, vv, B, red);
+  for (int b = tid; b < B; b += kThreads) {
+    p.vf[pb + b] = df_to_float(vv[b]);
+    stf(p.zt, pb + b, Z1[b]);
+    stf(p.tprev, pb + b, U1[b]);
+    stf(p.muk, pb + b, vmk[b]);
+  }
+  if (tid == 0) {
+    float4* ps = reinterpret_cast<float4*>(p.pscal) + part;
+    const float4 old = *ps;
+    *ps = make_float4(df_to_float(q), df_to_float(muv), df_to_float(coff), old.w);
+    double* dsw = p.dscal + (size_t)part * 4;
+    dsw[DS_BBAR] = df_to_double(bbar);
+    dsw[DS_Q] = df_to_double(q);
+    if (!(q.hi > 0.f) || !df_isfinite(q)) p.status[part] = MF_ERR_NOT_SPD;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ df red[kWarps];
+  __shared__ int s_flag;
+  const int part = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int B = p.B, BA = p.BA;
+  const size_t pb = (size_t)part * B;
+  if (p.status[part] != MF_OK) return;
+  df* A = reinterpret_cast<df*>(smem_raw);
+  df* u1 = A + (size_t)BA * BA;  // mu0f
+  df* u2 = u1 + B;               // t^k
+  df* u3 = u2 + B;               // mu0f - mu^k
+  df* vz = u3 + B;
+  df* invd = vz + B;
+  df* vd = invd + B;             // mu^k - mu0f
+
+  reduce_k1(p, part, A);
+  const df N = A[(B + 2) * BA + B + 2];
+  const df invN = df_recip(N);
+  for (int b = tid; b < B; b += kThreads) {
+    const df mf{p.mu0f[pb + b], 0.f};
+    const df mk = ldf(p.muk, pb + b);
+    u1[b] = mf;
+    u2[b] = ldf(p.tprev, pb + b);
+    u3[b] = df_sub(mf, mk);
+    vd[b] = df_sub(mk, mf);
+    vz[b] = u2[b];
+  }
+  __syncthreads();
+  assemble(p, A, u1, u2, u3, invN, nullptr);
+  if (!cholesky_df(A, B, BA, invd, &s_flag)) {
+    fail_partition(p, part, false);
+    return;
+  }
+  chol_solve_df(A, B, BA, invd, vz);
+  const df q = block_dot_df(u2, vz, B, red);
+  const df muv = block_dot_df(u1, vz, B, red);
+  const df coff = block_dot_df(vd, vz, B, red);
+  for (int b = tid; b < B; b += kThreads) p.vf[pb + b] = df_to_float(vz[b]);
+  if (tid == 0) {
+    float4* ps = reinterpret_cast<float4*>(p.pscal) + part;
+    const float4 old = *ps;
+    *ps = make_float4(df_to_float(q), df_to_float(muv), df_to_float(coff), old.w);
+    p.dscal[(size_t)part * 4 + DS_Q] = df_to_double(q);
+    if (!(q.hi > 0.f) || !df_isfinite(q)) p.status[part] = MF_ERR_NOT_SPD;
+  }
+}
+
+cudaError_t solve_set_attributes(size_t s_init, size_t s_iter, size_t s_lit) {
+  cudaError_t e = cudaFuncSetAttribute(solve_init_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_init);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(solve_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)s_iter);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(solve_literal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)s_lit);
+}
+
+void solve_init_launch(size_t smem, cudaStream_t s, const Params& p) {
+  solve_init_kernel<<<p.P, kThreads, smem, s>>>(p);
+}
+void solve_iter_launch(size_t smem, cudaStream_t s, const Params& p, int mode) {
+  solve_iter_kernel<<<p.P, kThreads, smem, s>>>(p, mode);
+}
+void solve_literal_launch(size_t smem, cudaStream_t s, const Params& p) {
+  solve_literal_kernel<<<p.P, kThreads, smem, s>>>(p);
+}
+
+}  // namespace mf

@@ -1,74 +1,102 @@
-// Statistics kernel: background mean and covariance of each partition.
+// Statistics kernel: second moments of the background of each partition.
 //
 // Fig. 1 (Algorithm AlbedoReWeightL1Filter) initialises mu^0 = (1/N) sum L_i
 // and C^0 = (1/N) sum (L_i - mu^0)(L_i - mu^0)^T (outer product, as in
 // Eq. (11)); the literal schedule recomputes C^k = (1/N) sum d_i d_i^T with
 // d_i = L_i - r_i alpha_i^{k-1} t(mu^k) - mu^k at every iteration.
 //
-// One pass over the cube.  Each pixel is split along a reference direction m
-// (the first valid pixel of the partition at initialisation, mu^0 afterwards):
+// One CTA streams one detector column over a chunk of rows: a TMA box of 128
+// rows x B bands per stage, double buffered on mbarriers.  Each pixel is
+// split along a reference direction m (the first valid pixel of the
+// partition at initialisation, mu^0 afterwards):
 //   x_i = rho_i m + e_i,  rho_i = x_i.m / m.m,
 // which removes the large albedo component (Sec. II-C) from what is
-// accumulated in float32: the CTA forms the augmented second moments of
+// accumulated in float32.  The CTA forms the augmented second moments of
 //   [e_i, a_i, b_i, 1],  a_i = rho_i - 1,  b_i = -r_i alpha_i^{k-1},
-// (a symmetric (B+3)x(B+3) product, 4x4 register blocks per thread), folds
-// each 128-pixel batch into float-float (TwoSum) accumulators and writes
-// them as float64.  The last CTA of a partition reduces all partial moments
-// in a fixed order in float64, assembles C exactly from them, factorises it
-// (Cholesky, float64) and solves C v = t.
+// a symmetric (B+3)x(B+3) product in 4x4 register blocks, folded every 32
+// pixels into double-float (TwoSum) accumulators, and writes them out.  The
+// solve kernel reduces them and assembles C exactly.
 #include "mf_common.cuh"
 #include "mf_pixel_io.cuh"
+#include "mf_tma.cuh"
 #include "../../include/mf.h"
 
 namespace mf {
 
-constexpr int kBatch = 128;
-
-size_t stats_smem_bytes(int B, int BA) {
-  const size_t stage = (size_t)kBatch * BA * sizeof(float);
-  const size_t tail = ((size_t)BA * BA + 8 * (size_t)B + 16) * sizeof(double);
-  return stage > tail ? stage : tail;
-}
-
-// thread t < nb(nb+1)/2 owns the 4x4 block (bi, bj), bi <= bj
-__device__ __forceinline__ void block_of(int t, int nb, int& bi, int& bj) {
-  int r = 0, rem = t;
-  while (rem >= nb - r) {
-    rem -= nb - r;
-    ++r;
-  }
-  bi = r;
-  bj = r + rem;
-}
+namespace {
+constexpr int kFold = 32;
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bp = s - hi;
-  const float err = (hi - (s - bp)) + (x - bp);
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
   hi = s;
-  lo += err;
+  lo = __fadd_rn(lo, err);
 }
 
-__device__ void stats_tail(const Params& p, int mode, int part, int ncp, const float* s_ref,
-                           double* sm, double* red, int* flag);
+struct StatSmem {
+  size_t stage_bytes, stages_off, coef_off, acc_off, bar_off, total;
+};
+// stages | coefficients [a, b, 1, 0] | double-float accumulators | barriers
+__host__ __device__ inline StatSmem stat_layout(int B) {
+  StatSmem L;
+  const int nb = (B + 4) / 4;
+  const size_t nblk = (size_t)nb * (nb + 1) / 2;
+  L.stage_bytes = (size_t)kStatRows * B * sizeof(float);
+  L.stages_off = 0;
+  L.coef_off = 2 * L.stage_bytes;
+  L.acc_off = L.coef_off + 2 * (size_t)kStatRows * 4 * sizeof(float);
+  L.bar_off = L.acc_off + nblk * 32 * sizeof(float);
+  L.total = L.bar_off + 4 * sizeof(uint64_t);
+  return L;
+}
+}  // namespace
+
+size_t stats_smem_bytes(int B) { return stat_layout(B).total + 128; }
 
 template <int NJ>
-__global__ void __launch_bounds__(kThreads) stats_kernel(Params p, int mode) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* stage = reinterpret_cast<float*>(smem_raw);
+__global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__ CUtensorMap map,
+                                                         Params p, int mode) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(16) float s_ref[kMaxB];
   __shared__ float s_inv_ref2;
-  __shared__ int s_last, s_flag, s_pilot;
-  __shared__ double s_red[kWarps];
+  __shared__ int s_pilot, s_abort;
 
-  int c, chunk;
-  unit_of_block(p, p.n_sc, c, chunk);
-  if (c >= p.cols) return;
+  const int c = blockIdx.x % p.cols;
+  const int chunk = blockIdx.x / p.cols;
   const int part = part_of(p, c);
   const int c0 = part * p.G;
   const int ncp = part_ncols(p, part);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int B = p.B, B4 = p.B4, BA = p.BA;
+  const StatSmem L = stat_layout(B);
+  float* stage[2] = {reinterpret_cast<float*>(smem_raw + L.stages_off),
+                     reinterpret_cast<float*>(smem_raw + L.stages_off + L.stage_bytes)};
+  float4* coef[2] = {reinterpret_cast<float4*>(smem_raw + L.coef_off),
+                     reinterpret_cast<float4*>(smem_raw + L.coef_off) + kStatRows};
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bar_off);
+
+  const int r_beg = chunk * p.sc_rows;
+  const int r_end = min(p.rows, r_beg + p.sc_rows);
+  const int nst = (r_end - r_beg + kStatRows - 1) / kStatRows;
+  const uint32_t box_bytes = (uint32_t)(kStatRows * B * sizeof(float));
+
+  if (tid == 0) {
+    s_abort = 0;
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int issued[2] = {0, 0};  // copies issued per stage buffer (thread 0)
+  if (tid == 0) {
+    prefetch_tmap(&map);
+    for (int s = 0; s < 2 && s < nst; ++s) {
+      mbar_arrive_expect_tx(&full[s], box_bytes);
+      tma_load_3d(stage[s], &map, p.band_lo, c, r_beg + s * kStatRows, &full[s]);
+      ++issued[s];
+    }
+  }
 
   // ---- reference direction m
   if (mode == STAT_INIT) {
@@ -96,11 +124,9 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(Params p, int mode) {
     const int pi = s_pilot;
     for (int b = tid; b < B; b += kThreads) {
       float v = 0.f;
-      if (pi >= 0) {
-        const int row = pi / ncp, col = c0 + pi % ncp;
-        v = pixel_ptr(p, row, col)[b];
-      }
+      if (pi >= 0) v = pixel_ptr(p, pi / ncp, c0 + pi % ncp)[b];
       s_ref[b] = v;
+      if (c == c0 && chunk == 0) p.pilot[(size_t)part * B + b] = v;
     }
   } else {
     for (int b = tid; b < B; b += kThreads) s_ref[b] = p.mu0f[(size_t)part * B + b];
@@ -112,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(Params p, int mode) {
       for (int b = 0; b < B; ++b) n2 += (double)s_ref[b] * s_ref[b];
       s_inv_ref2 = n2 > 0.0 ? (float)(1.0 / n2) : 0.f;
     } else {
-      s_inv_ref2 = (float)p.scal[(size_t)part * SC_NSCAL + SC_INVMU2];
+      s_inv_ref2 = p.pscal[(size_t)part * PS_N + PS_INVMU2];
     }
   }
   __syncthreads();
@@ -120,229 +146,115 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(Params p, int mode) {
   const float4* ref4 = reinterpret_cast<const float4*>(s_ref);
   const bool albedo = (p.flags & MF_ALBEDO) != 0;
 
-  // ---- SYRK ownership
+  // ---- SYRK ownership: 4x4 blocks of the upper triangle, blocks tid,
+  // tid + 256, ...; double-float accumulators in shared memory, block-major
+  // with the 32 floats (16 hi, 16 lo) of a block strided by nblk
   const int nb = BA / 4;
   const int nblk = nb * (nb + 1) / 2;
-  int bi = 0, bj = 0;
-  const bool syrk = tid < nblk;
-  if (syrk) block_of(tid, nb, bi, bj);
-  float hi[16], lo[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0.f;
+  const int bcoef = B / 4;  // block index of [a, b, 1, 0]
+  float* accs = reinterpret_cast<float*>(smem_raw + L.acc_off);
+  for (int q = tid; q < nblk * 32; q += kThreads) accs[q] = 0.f;
 
-  const int r_beg = chunk * p.sc_rows;
-  const int r_end = min(p.rows, r_beg + p.sc_rows);
   const int e = lane & 1;
-  const int slot = warp * 16 + (lane >> 1);
-  for (int r0 = r_beg; r0 < r_end; r0 += kBatch) {
-    // stage the augmented vectors [e_i, a_i, b_i, 1] of 128 pixels
+  const int slot = warp * 16 + (lane >> 1);  // 0..127
+  for (int i = 0; i < nst; ++i) {
+    const int sb = i & 1;
+    if (!mbar_wait(&full[sb], (uint32_t)((i >> 1) & 1))) {
+      if (lane == 0) atomicExch(&s_abort, 1);
+    }
+    __syncthreads();
+    if (s_abort) break;
+    // phase A: residuals e_i in place, coefficients [a, b, 1, 0]
     {
-      const int row = r0 + slot;
+      const int row = r_beg + i * kStatRows + slot;
       const bool inb = row < r_end;
+      float* px = stage[sb] + (size_t)slot * B;
       float4 x[NJ];
-      const bool fin = load_pixel<NJ>(p, row, c, inb, e, x);
+      const bool fin = lds_pixel<NJ>(px, inb, e, B4, x);
       const size_t pix = (size_t)(inb ? row : 0) * p.cols + c;
       const bool valid = inb && fin && (!p.mask || p.mask[pix] == 0);
       const float rho = pair_dot<NJ>(x, ref4, e, B4) * inv_ref2;
       split_residual<NJ>(x, ref4, rho, e, B4);
-      float bcoef = 0.f;
-      if (mode == STAT_LITERAL && valid) {
-        const float r = albedo ? rho : 1.f;
-        bcoef = r > 0.f ? -(r * p.alpha[pix]) : 0.f;
-      }
-      float* dst = stage + (size_t)slot * BA;
+      if (!valid) {
 #pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const int f = e + 2 * j;
-        if (f < B4) {
-          float4 v = valid ? x[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-          *reinterpret_cast<float4*>(dst + 4 * f) = v;
-        }
+        for (int j = 0; j < NJ; ++j) x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      sts_pixel<NJ>(px, e, B4, x);
       if (e == 0) {
-        dst[B] = valid ? rho - 1.f : 0.f;
-        dst[B + 1] = valid ? bcoef : 0.f;
-        dst[B + 2] = valid ? 1.f : 0.f;
-        for (int q = B + 3; q < BA; ++q) dst[q] = 0.f;
+        float bcf = 0.f;
+        if (mode == STAT_LITERAL && valid) {
+          const float r = albedo ? rho : 1.f;
+          bcf = r > 0.f ? -(r * p.alpha[pix]) : 0.f;
+        }
+        coef[sb][slot] = valid ? make_float4(rho - 1.f, bcf, 1.f, 0.f)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     __syncthreads();
-    if (syrk) {
-      float acc[16];
+    // phase B: augmented SYRK over the 128 pixels of the stage
+    for (int blk = tid; blk < nblk; blk += kThreads) {
+      int bi, bj;
+      block_of(blk, nb, bi, bj);
+      // row pointers and strides: the [a, b, 1, 0] block lives in coef[]
+      const float* pa = (bi == bcoef) ? reinterpret_cast<const float*>(coef[sb]) : stage[sb] + 4 * bi;
+      const float* pb = (bj == bcoef) ? reinterpret_cast<const float*>(coef[sb]) : stage[sb] + 4 * bj;
+      const int sa = (bi == bcoef) ? 4 : B;
+      const int sbs = (bj == bcoef) ? 4 : B;
+      float hi[16], lo[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-      const float* col_i = stage + 4 * bi;
-      const float* col_j = stage + 4 * bj;
+      for (int q = 0; q < 16; ++q) {
+        hi[q] = accs[q * nblk + blk];
+        lo[q] = accs[(16 + q) * nblk + blk];
+      }
+      for (int s0 = 0; s0 < kStatRows; s0 += kFold) {
+        float acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0.f;
 #pragma unroll 4
-      for (int s = 0; s < kBatch; ++s) {
-        const float4 va = *reinterpret_cast<const float4*>(col_i + (size_t)s * BA);
-        const float4 vb = *reinterpret_cast<const float4*>(col_j + (size_t)s * BA);
-        const float a4[4] = {va.x, va.y, va.z, va.w};
-        const float b4[4] = {vb.x, vb.y, vb.z, vb.w};
+        for (int s = s0; s < s0 + kFold; ++s) {
+          const float4 va = *reinterpret_cast<const float4*>(pa + (size_t)s * sa);
+          const float4 vb = *reinterpret_cast<const float4*>(pb + (size_t)s * sbs);
+          const float a4[4] = {va.x, va.y, va.z, va.w};
+          const float b4[4] = {vb.x, vb.y, vb.z, vb.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int w = 0; w < 4; ++w) acc[u * 4 + w] = fmaf(a4[u], b4[w], acc[u * 4 + w]);
+            for (int w = 0; w < 4; ++w) acc[u * 4 + w] = fmaf(a4[u], b4[w], acc[u * 4 + w]);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) two_sum_acc(hi[q], lo[q], acc[q]);
       }
 #pragma unroll
-      for (int i = 0; i < 16; ++i) two_sum_acc(hi[i], lo[i], acc[i]);
+      for (int q = 0; q < 16; ++q) {
+        accs[q * nblk + blk] = hi[q];
+        accs[(16 + q) * nblk + blk] = lo[q];
+      }
     }
     __syncthreads();
-  }
-
-  // ---- publish this CTA's moments
-  const int K1E = k1_entries(BA);
-  const int unit = (c - c0) * p.n_sc + chunk;
-  double* dst = p.k1part + ((size_t)part * p.G * p.n_sc + unit) * K1E;
-  if (syrk) {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) dst[tid * 16 + i] = (double)hi[i] + (double)lo[i];
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    const unsigned prev = atomicAdd(&p.counters[part], 1u);
-    s_last = (prev + 1u == (unsigned)(ncp * p.n_sc)) ? 1 : 0;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  stats_tail(p, mode, part, ncp, s_ref, reinterpret_cast<double*>(smem_raw), s_red, &s_flag);
-  if (tid == 0) p.counters[part] = 0u;
-}
-
-// Reduce the partition's partial moments, assemble C, factorise, solve C v = t.
-__device__ void stats_tail(const Params& p, int mode, int part, int ncp, const float* s_ref,
-                           double* sm, double* red, int* flag) {
-  const int tid = threadIdx.x;
-  const int B = p.B, BA = p.BA;
-  const int K1E = k1_entries(BA);
-  const int nb = BA / 4;
-  double* A = sm;                    // BA x BA
-  double* u1 = A + (size_t)BA * BA;  // reference direction
-  double* u2 = u1 + B;               // target t^k (literal) / 0
-  double* u3 = u2 + B;               // u1 - mu
-  double* mu = u3 + B;               // mean of the statistics
-  double* vz = mu + B;               // right-hand side / solution
-  double* id = vz + B;               // 1 / diag(L)
-  double* tt = id + B;               // target of the solve
-
-  const int nunits = ncp * p.n_sc;
-  const double* P0 = p.k1part + (size_t)part * p.G * p.n_sc * K1E;
-  for (int q = tid; q < K1E; q += kThreads) {
-    double s = 0.0;
-    for (int u = 0; u < nunits; ++u) s += __ldcg(P0 + (size_t)u * K1E + q);
-    const int t = q >> 4, w = q & 15;
-    int bi, bj;
-    block_of(t, nb, bi, bj);
-    const int i = 4 * bi + (w >> 2), j = 4 * bj + (w & 3);
-    A[i * BA + j] = s;
-    A[j * BA + i] = s;
-  }
-  __syncthreads();
-  const double N = A[(B + 2) * BA + (B + 2)];
-  const bool enough = N > (double)B;
-  const double iN = enough ? 1.0 / N : 0.0;
-  const size_t pb = (size_t)part * B;
-  for (int b = tid; b < B; b += kThreads) {
-    if (mode == STAT_INIT) {
-      const double m = (double)s_ref[b];
-      u1[b] = m;
-      u2[b] = 0.0;
-      mu[b] = m + (A[b * BA + B + 2] + A[B * BA + B + 2] * m) * iN;
-      u3[b] = m - mu[b];
-    } else {
-      u1[b] = (double)p.mu0f[pb + b];
-      u2[b] = p.tprev[pb + b];
-      mu[b] = p.muk[pb + b];
-      u3[b] = u1[b] - mu[b];
+    if (tid == 0 && i + 2 < nst) {
+      fence_proxy_async_smem();  // phase A wrote this buffer through the generic proxy
+      mbar_arrive_expect_tx(&full[sb], box_bytes);
+      tma_load_3d(stage[sb], &map, p.band_lo, c, r_beg + (i + 2) * kStatRows, &full[sb]);
+      ++issued[sb];
     }
   }
-  __syncthreads();
-  // C = (1/N) sum (e + a u1 + b u2 + u3)(...)^T, expanded over the moments
-  const double aa = A[B * BA + B], ab = A[B * BA + B + 1], bb = A[(B + 1) * BA + B + 1];
-  const double a1 = A[B * BA + B + 2], b1 = A[(B + 1) * BA + B + 2];
-  const double n1 = A[(B + 2) * BA + B + 2];
-  for (int idx = tid; idx < B * B; idx += kThreads) {
-    const int i = idx / B, j = idx % B;
-    double v = A[i * BA + j];
-    v += A[i * BA + B] * u1[j] + u1[i] * A[j * BA + B];
-    v += A[i * BA + B + 1] * u2[j] + u2[i] * A[j * BA + B + 1];
-    v += A[i * BA + B + 2] * u3[j] + u3[i] * A[j * BA + B + 2];
-    v += aa * u1[i] * u1[j] + ab * (u1[i] * u2[j] + u2[i] * u1[j]) + bb * u2[i] * u2[j];
-    v += a1 * (u1[i] * u3[j] + u3[i] * u1[j]) + b1 * (u2[i] * u3[j] + u3[i] * u2[j]);
-    v += n1 * u3[i] * u3[j];
-    A[i * BA + j] = v * iN;
-  }
-  __syncthreads();
-  double* Sg = p.S + (size_t)part * B * B;
-  if (mode == STAT_INIT) {
-    for (int idx = tid; idx < B * B; idx += kThreads) Sg[idx] = A[(idx / B) * BA + idx % B];
-  }
-  const bool ok = enough && block_cholesky(A, B, BA, id, flag);
-  double* scal = p.scal + (size_t)part * SC_NSCAL;
-  if (!ok) {
-    for (int b = tid; b < B; b += kThreads) {
-      p.vf[pb + b] = 0.f;
-      if (mode == STAT_INIT) {
-        p.mu0f[pb + b] = 0.f;
-        p.mu0d[pb + b] = 0.0;
-        p.tprev[pb + b] = 0.0;
-      }
-    }
+  if (s_abort) {
     if (tid == 0) {
-      p.status[part] = MF_ERR_NOT_SPD;
-      scal[SC_Q] = 1.0;
-      scal[SC_MUV] = 0.0;
-      scal[SC_COFF] = 0.0;
-      if (mode == STAT_INIT) {
-        scal[SC_N] = N;
-        scal[SC_INVMU2] = 0.0;
-      }
+      // bounded wait for the last copy issued on each buffer before the CTA exits
+      for (int s = 0; s < 2; ++s)
+        if (issued[s] > 0) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1));
+      p.status[part] = MF_ERR_TIMEOUT;
     }
     return;
   }
-  double* Lg = p.L + (size_t)part * B * B;
-  for (int idx = tid; idx < B * B; idx += kThreads) {
-    const int i = idx / B, j = idx % B;
-    Lg[idx] = (j <= i) ? A[i * BA + j] : 0.0;
-  }
-  for (int b = tid; b < B; b += kThreads) {
-    p.invd[pb + b] = id[b];
-    const double t = (mode == STAT_INIT) ? mu[b] * (double)p.k[b] : u2[b];
-    tt[b] = t;
-    vz[b] = t;
-  }
-  block_chol_solve(A, B, BA, id, vz, B, 1);
-  // mu0f as the pixel kernel will hold it
-  for (int b = tid; b < B; b += kThreads) {
-    if (mode == STAT_INIT) {
-      const float mf = (float)mu[b];
-      p.mu0f[pb + b] = mf;
-      p.mu0d[pb + b] = mu[b];
-      p.tprev[pb + b] = tt[b];
-      u1[b] = (double)mf;           // now mu0f
-    }
-    u3[b] = mu[b] - u1[b];          // mu^k - mu0f
-  }
-  __syncthreads();
-  const double q = block_dot(tt, vz, B, red);
-  const double muv = block_dot(u1, vz, B, red);
-  const double coff = block_dot(u3, vz, B, red);
-  const double n2 = block_dot(u1, u1, B, red);
-  for (int b = tid; b < B; b += kThreads) p.vf[pb + b] = (float)vz[b];
-  if (tid == 0) {
-    scal[SC_Q] = q;
-    scal[SC_MUV] = muv;
-    scal[SC_COFF] = coff;
-    if (mode == STAT_INIT) {
-      scal[SC_N] = N;
-      scal[SC_INVMU2] = n2 > 0.0 ? 1.0 / n2 : 0.0;
-      scal[SC_BBAR] = 0.0;
-      p.status[part] = (q > 0.0 && isfinite(q)) ? MF_OK : MF_ERR_NOT_SPD;
-    } else if (!(q > 0.0 && isfinite(q))) {
-      p.status[part] = MF_ERR_NOT_SPD;
-    }
+
+  // ---- publish this CTA's moments (double-float pairs)
+  const int K1E = k1_entries(BA);
+  const int unit = (c - c0) * p.n_sc + chunk;
+  float2* dst = p.k1part + ((size_t)part * p.G * p.n_sc + unit) * K1E;
+  for (int q = tid; q < nblk * 16; q += kThreads) {
+    const int blk = q >> 4, w = q & 15;
+    dst[q] = make_float2(accs[w * nblk + blk], accs[(16 + w) * nblk + blk]);
   }
 }
 
@@ -358,10 +270,11 @@ cudaError_t stats_set_attributes(int nj, size_t smem) {
   return cudaErrorInvalidValue;
 }
 
-void stats_launch(int nj, int grid, size_t smem, cudaStream_t s, const Params& p, int mode) {
+void stats_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
+                  const Params& p, int mode) {
 #define MF_CASE(NJ)                                                   \
   case NJ:                                                            \
-    stats_kernel<NJ><<<grid, kThreads, smem, s>>>(p, mode);           \
+    stats_kernel<NJ><<<grid, kThreads, smem, s>>>(map, p, mode);      \
     return;
   switch (nj) { MF_NJ_CASES(MF_CASE) }
 #undef MF_CASE
