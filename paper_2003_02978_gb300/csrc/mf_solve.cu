@@ -36,6 +36,10 @@ __device__ __forceinline__ df shfl_xor_df(df v, int o) {
   return df{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }
 
+__device__ __forceinline__ df shfl_df(df v, int src) {
+  return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
 // CTA-wide double-float sum, fixed order; every thread gets the result
 __device__ df block_sum_df(df v, df* red) {
 #pragma unroll
@@ -62,6 +66,28 @@ struct Dot2 {
   }
   __device__ __forceinline__ df result() const { return fast_two_sum(s, c); }
 };
+
+// dot product of length n by one warp (lanes stride the index), all lanes
+// get the result
+__device__ __forceinline__ df warp_dot_df(const df* a, const df* b, int n) {
+  Dot2 d;
+  for (int i = threadIdx.x & 31; i < n; i += 32) d.add(a[i], b[i]);
+  df v = d.result();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_xor_df(v, o));
+  return v;
+}
+
+// several dots at once: dot t (t < nd) = a[t] . b[t], one warp per dot,
+// written to out[t]; one barrier
+__device__ void multi_dot_df(const df* const* a, const df* const* b, int nd, int n, df* out) {
+  const int w = threadIdx.x >> 5;
+  for (int t = w; t < nd; t += kWarps) {
+    const df v = warp_dot_df(a[t], b[t], n);
+    if ((threadIdx.x & 31) == 0) out[t] = v;
+  }
+  __syncthreads();
+}
 
 __device__ df block_dot_df(const df* a, const df* b, int n, df* red) {
   Dot2 d;
@@ -127,28 +153,29 @@ __device__ void assemble(const Params& p, df* A, const df* u1, const df* u2, con
 }
 
 // In-place Cholesky of the lower triangle of the leading n x n block (row
-// stride ld): right-looking, one column per step.  invd[j] = 1 / L_jj.
-// Returns false (uniformly) if a pivot is not > 0.
+// stride ld): right-looking, one column per step and one barrier per step.
+// Step j reads the pivot d = A_jj (final since step j-1), updates the
+// trailing block with the unscaled column j times 1/d, and scales column
+// j-1 by its 1/L (column j-1 is no longer read).  invd[j] = 1/L_jj; the
+// diagonal of L is written after the loop (no step reads it).  Returns false
+// (uniformly) if a pivot is not > 0.
 __device__ bool cholesky_df(df* A, int n, int ld, df* invd, int* flag) {
   const int tid = threadIdx.x;
-  if (tid == 0) *flag = 0;
+  (void)flag;
+  bool ok = true;
+  __syncthreads();
   for (int j = 0; j < n; ++j) {
-    __syncthreads();
-    if (tid == 0) {
-      const df d = A[j * ld + j];
-      if (!(d.hi > 0.f) || !df_isfinite(d)) {
-        *flag = 1;
-      } else {
-        const df r = df_rsqrt(d);
-        A[j * ld + j] = df_mul(d, r);
-        invd[j] = r;
-      }
+    const df d = A[j * ld + j];
+    if (!(d.hi > 0.f) || !df_isfinite(d)) {
+      ok = false;  // uniform: every thread reads the same pivot
+      break;
     }
-    __syncthreads();
-    if (*flag) return false;
-    const df r = invd[j];
-    for (int i = j + 1 + tid; i < n; i += kThreads) A[i * ld + j] = df_mul(A[i * ld + j], r);
-    __syncthreads();
+    const df r = df_rsqrt(d);        // 1/sqrt(d), same in every thread
+    const df rinv = df_mul(r, r);    // 1/d
+    if (j > 0) {
+      const df rp = invd[j - 1];
+      for (int i = j + tid; i < n; i += kThreads) A[i * ld + j - 1] = df_mul(A[i * ld + j - 1], rp);
+    }
     const int m = n - j - 1;
     const int cnt = m * (m + 1) / 2;
     for (int idx = tid; idx < cnt; idx += kThreads) {
@@ -157,16 +184,22 @@ __device__ bool cholesky_df(df* A, int n, int ld, df* invd, int* flag) {
       while ((ii + 1) * (ii + 2) / 2 <= idx) ++ii;
       const int kk = idx - ii * (ii + 1) / 2;
       const int i = j + 1 + ii, k = j + 1 + kk;
-      A[i * ld + k] = df_sub(A[i * ld + k], df_mul(A[i * ld + j], A[k * ld + j]));
+      A[i * ld + k] = df_sub(A[i * ld + k], df_mul(df_mul(A[i * ld + j], A[k * ld + j]), rinv));
     }
+    if (tid == 0) invd[j] = r;
+    __syncthreads();
   }
+  if (!ok) return false;
+  for (int j = tid; j < n; j += kThreads) A[j * ld + j] = df_recip(invd[j]);
   __syncthreads();
   return true;
 }
 
 // X = L^{-1} stored transposed in the strict upper triangle of A
 // (A[j][i] = X[i][j], j < i); X's diagonal is invd.  Right-looking row
-// elimination of L X = I.
+// elimination of L X = I, one barrier per step: step i updates the rows
+// below with the still unscaled row i times 1/L_ii, and scales row i-1
+// (no longer read).
 __device__ void tri_inverse_df(df* A, int n, int ld, const df* invd) {
   const int tid = threadIdx.x;
   for (int idx = tid; idx < n * n; idx += kThreads) {
@@ -175,16 +208,24 @@ __device__ void tri_inverse_df(df* A, int n, int ld, const df* invd) {
   }
   __syncthreads();
   for (int i = 0; i < n; ++i) {
-    for (int j = tid; j < i; j += kThreads) A[j * ld + i] = df_mul(A[j * ld + i], invd[i]);
-    __syncthreads();
+    const df di = invd[i];
+    if (i > 0) {
+      const df dp = invd[i - 1];
+      for (int j = tid; j < i - 1; j += kThreads) A[j * ld + i - 1] = df_mul(A[j * ld + i - 1], dp);
+    }
     const int rows = n - i - 1, cols = i + 1;
     for (int idx = tid; idx < rows * cols; idx += kThreads) {
       const int r = i + 1 + idx / cols, j = idx % cols;
-      const df xij = (j == i) ? invd[i] : A[j * ld + i];
+      // X[i][j] = invd_i * R[i][j] (j < i), X[i][i] = invd_i
+      const df xij = (j == i) ? di : df_mul(A[j * ld + i], di);
       A[j * ld + r] = df_sub(A[j * ld + r], df_mul(A[r * ld + i], xij));
     }
     __syncthreads();
   }
+  // deferred scaling of the last row
+  const df dl = invd[n - 1];
+  for (int j = tid; j < n - 1; j += kThreads) A[j * ld + n - 1] = df_mul(A[j * ld + n - 1], dl);
+  __syncthreads();
 }
 
 // solve (L L^T) x = b in place (single right-hand side), L lower in A
@@ -455,40 +496,75 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
   // C0^{-1} (t^k - t^{k+1}) = z(t^k) - z(t^{k+1})
   for (int b = tid; b < B; b += kThreads) Z2[b] = df_sub(ldf(p.zt, pb + b), Z1[b]);
   __syncthreads();
-  const df* Uc[3] = {U0, U1, U2};
-  const df* Zc[3] = {Z0, Z1, Z2};
-  df W[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) W[a][c] = block_dot_df(Uc[a], Zc[c], B, red);
-  if (tid == 0) {
-    // C = C0 + U M U^T;  v = z_t - Z (I + M W)^{-1} M W[:, 1]
-    const df zero{0.f, 0.f}, one{1.f, 0.f}, mone{-1.f, 0.f};
-    const df M[3][3] = {{zero, mone, zero}, {mone, var, zero}, {zero, zero, df_mul(bbar, bbar)}};
-    df A3[3][3], rhs[3], y[3];
-    for (int i = 0; i < 3; ++i) {
-      rhs[i] = zero;
-      for (int j = 0; j < 3; ++j) {
-        df s = (i == j) ? one : zero;
-        for (int k = 0; k < 3; ++k) s = df_fma(M[i][k], W[k][j], s);
-        A3[i][j] = s;
-        rhs[i] = df_fma(M[i][j], W[j][1], rhs[i]);
+  __shared__ df s_W[9];
+  __shared__ df s_A3[9];
+  __shared__ df s_rhs[3];
+  {
+    const df* ua[9] = {U0, U0, U0, U1, U1, U1, U2, U2, U2};
+    const df* zb[9] = {Z0, Z1, Z2, Z0, Z1, Z2, Z0, Z1, Z2};
+    multi_dot_df(ua, zb, 9, B, s_W);
+  }
+  // C = C0 + U M U^T;  v = z_t - Z (I + M W)^{-1} M W[:, 1].  Warp 0: lane
+  // (i, j) < 9 forms (I + M W)_ij, then the 3x3 system by Cramer's rule.
+  if (tid < 32) {
+    const int lane = tid;
+    const df zero{0.f, 0.f};
+    const df mb2 = df_mul(bbar, bbar);
+    // M = [[0, -1, 0], [-1, var, 0], [0, 0, mean(beta)^2]]
+    auto Mrow = [&](int i, int k) -> df {
+      if (i == 0) return k == 1 ? df{-1.f, 0.f} : zero;
+      if (i == 1) return k == 0 ? df{-1.f, 0.f} : (k == 1 ? var : zero);
+      return k == 2 ? mb2 : zero;
+    };
+    if (lane < 9) {
+      const int i = lane / 3, j = lane % 3;
+      df a = (i == j) ? df{1.f, 0.f} : zero;
+      for (int k = 0; k < 3; ++k) a = df_fma(Mrow(i, k), s_W[k * 3 + j], a);
+      s_A3[lane] = a;
+    } else if (lane < 12) {
+      const int i = lane - 9;
+      df r = zero;
+      for (int k = 0; k < 3; ++k) r = df_fma(Mrow(i, k), s_W[k * 3 + 1], r);
+      s_rhs[i] = r;
+    }
+    __syncwarp();
+    // cofactors C_ij of A3 (lane i*3+j), determinant along row 0
+    df cof = zero;
+    if (lane < 9) {
+      const int i = lane / 3, j = lane % 3;
+      const int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
+      cof = df_sub(df_mul(s_A3[r0 * 3 + c0], s_A3[r1 * 3 + c1]),
+                   df_mul(s_A3[r0 * 3 + c1], s_A3[r1 * 3 + c0]));
+    }
+    const df c00 = shfl_df(cof, 0), c01 = shfl_df(cof, 1), c02 = shfl_df(cof, 2);
+    df det = df_mul(s_A3[0], c00);
+    det = df_fma(s_A3[1], c01, det);
+    det = df_fma(s_A3[2], c02, det);
+    // y_i = sum_j C_ji rhs_j / det  (adjugate = transposed cofactors); all
+    // lanes take part in the shuffles
+    const df cf[9] = {shfl_df(cof, 0), shfl_df(cof, 1), shfl_df(cof, 2), shfl_df(cof, 3),
+                      shfl_df(cof, 4), shfl_df(cof, 5), shfl_df(cof, 6), shfl_df(cof, 7),
+                      shfl_df(cof, 8)};
+    if (lane < 3) {
+      const int i = lane;
+      df num = df_mul(cf[0 * 3 + i], s_rhs[0]);
+      num = df_fma(cf[1 * 3 + i], s_rhs[1], num);
+      num = df_fma(cf[2 * 3 + i], s_rhs[2], num);
+      s_y[i] = df_div(num, det);
+    }
+    if (lane == 0) {
+      // Hadamard ratio |det| / prod ||row||: near 0 when I + M W is close to
+      // singular, i.e. C^{k+1} is far more singular than C^0 along U; the
+      // Woodbury form then loses the digits that a direct factorisation keeps
+      float hr = 1.f;
+      for (int i = 0; i < 3; ++i) {
+        float n2 = 0.f;
+        for (int j = 0; j < 3; ++j) n2 = fmaf(s_A3[i * 3 + j].hi, s_A3[i * 3 + j].hi, n2);
+        hr *= sqrtf(n2);
       }
+      hr = fabsf(det.hi) / fmaxf(hr, 1e-30f);
+      s_bad = (!(det.hi > 0.f) || !df_isfinite(det)) ? 1 : (hr < 1e-8f ? 2 : 0);
     }
-    // Hadamard ratio |det| / prod ||row||: near 0 when I + M W is close to
-    // singular, i.e. C^{k+1} is far more singular than C^0 along U; the
-    // Woodbury form then loses the digits that a direct factorisation keeps
-    float hr = 1.f;
-    for (int i = 0; i < 3; ++i) {
-      float n2 = 0.f;
-      for (int j = 0; j < 3; ++j) n2 = fmaf(A3[i][j].hi, A3[i][j].hi, n2);
-      hr *= sqrtf(n2);
-    }
-    const df det = solve3_df(A3, rhs, y);
-    hr = fabsf(det.hi) / fmaxf(hr, 1e-30f);
-    s_bad = !(det.hi > 0.f) || !df_isfinite(det) ? 1 : (hr < 1e-8f ? 2 : 0);
-    s_y[0] = y[0];
-    s_y[1] = y[1];
-    s_y[2] = y[2];
   }
   __syncthreads();
   if (s_bad == 1) {
@@ -527,9 +603,13 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
   }
   for (int b = tid; b < B; b += kThreads) U2[b] = df_sub(vmk[b], vmf[b]);  // mu^{k+1} - mu0f
   __syncthreads();
-  const df q = block_dot_df(U1, vv, B, red);
-  const df muv = block_dot_df(vmf, vv, B, red);
-  const df coff = block_dot_df(U2, vv, B, red);
+  __shared__ df s_d3[3];
+  {
+    const df* da[3] = {U1, vmf, U2};
+    const df* db[3] = {vv, vv, vv};
+    multi_dot_df(da, db, 3, B, s_d3);
+  }
+  const df q = s_d3[0], muv = s_d3[1], coff = s_d3[2];
   for (int b = tid; b < B; b += kThreads) {
     p.vf[pb + b] = df_to_float(vv[b]);
     stf(p.zt, pb + b, Z1[b]);
