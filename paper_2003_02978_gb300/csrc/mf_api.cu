@@ -84,10 +84,18 @@ int nj_bucket(int B4) {
   return -1;
 }
 
+// The shared-memory limit is an attribute of the kernel function, shared by
+// every plan whose band count falls in the same template bucket (and every
+// plan for the solve kernels): set it to the largest size any such plan needs.
 cudaError_t set_attrs(const mf_plan_s* pl) {
-  cudaError_t e = mf::stats_set_attributes(pl->nj, pl->smem_stats);
-  if (e == cudaSuccess) e = mf::pixel_set_attributes(pl->nj, pl->smem_pixel);
-  if (e == cudaSuccess) e = mf::solve_set_attributes(pl->smem_sinit, pl->smem_siter, pl->smem_slit);
+  const int bmax_bucket = 8 * pl->nj;
+  const int bmax = mf::kMaxB;
+  const int ba = (bmax + 3 + 3) / 4 * 4;
+  cudaError_t e = mf::stats_set_attributes(pl->nj, mf::stats_smem_bytes(bmax_bucket));
+  if (e == cudaSuccess) e = mf::pixel_set_attributes(pl->nj, mf::pixel_smem_bytes(bmax_bucket));
+  if (e == cudaSuccess)
+    e = mf::solve_set_attributes(mf::solve_init_smem_bytes(bmax, ba), mf::solve_iter_smem_bytes(bmax),
+                                 mf::solve_literal_smem_bytes(bmax, ba));
   return e;
 }
 
