@@ -139,6 +139,29 @@ mf_status mf_profile(mf_plan_t plan, int32_t enable);
  * arrays).  Synchronises the plan's last stream. */
 mf_status mf_profile_read(mf_plan_t plan, double* ms, int64_t* launches, int32_t n_kinds);
 
+/* Initial background statistics of every partition -- the mean mu^0 and
+ * covariance C^0 of Fig. 1's initialisation, as mf_background returns them
+ * after a retrieval -- without allocating any device memory.  The paper has
+ * no counterpart: this exists for callers that cannot allocate once running
+ * (graph-replayed pipelines with a fixed memory plan, real-time processing
+ * that forbids allocation after start-up, hosts whose device memory belongs
+ * to another allocator), which therefore cannot create a plan.
+ *   desc   shape, band window and col_group (flags and precision unused)
+ *   cube   device (rows, cols, bands_total) float32 BIP, 16-byte aligned
+ *   mask   device (rows, cols) uint8, nonzero = excluded, or NULL
+ *   mu0    device (P, B) float64 output;  cov0 device (P, B, B) float64 output
+ *          (NaN for a partition with N <= B valid pixels)
+ * The per-block partial moments live in a fixed 64 MiB file-scope device
+ * array that every GPU loading the library holds until exit; shapes whose
+ * moments do not fit (P * col_group * 8 * K bytes, K = 16 * nb (nb + 1) / 2,
+ * nb = (B + 4) / 4; about 24 KB per detector column at B = 72) return
+ * MF_ERR_UNSUPPORTED.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) and sets kernel attributes: make it
+ * before any stream capture.  Calls share the array: calls that overlap on
+ * the GPU race.  Enqueued on `stream`, no synchronisation. */
+mf_status mf_background_noalloc(const mf_desc* desc, const float* cube, const uint8_t* mask,
+                                double* mu0, double* cov0, void* stream);
+
 /* Static description of a status code. */
 const char* mf_status_string(mf_status s);
 

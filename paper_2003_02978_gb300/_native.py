@@ -54,6 +54,8 @@ def lib() -> ctypes.CDLL:
     L.mf_status_string.restype = c_char_p
     L.mf_last_error.argtypes = []
     L.mf_last_error.restype = c_char_p
+    L.mf_background_noalloc.argtypes = [POINTER(MfDesc), fp, fp, fp, fp, c_void_p]
+    L.mf_background_noalloc.restype = c_int
     for name, args in (("mf_profile", [c_void_p, c_int32]),
                        ("mf_profile_read", [c_void_p, POINTER(c_double), POINTER(c_int64),
                                             c_int32])):

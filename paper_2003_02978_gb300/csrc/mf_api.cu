@@ -46,6 +46,10 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+namespace mf {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace mf
+
 struct mf_plan_s {
   mf_desc d{};
   mf::Params prm{};       // geometry + workspace pointers; per-call fields set in retrieve

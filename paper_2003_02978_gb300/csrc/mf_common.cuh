@@ -127,5 +127,14 @@ void pixel_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorM
 void solve_init_launch(size_t smem, cudaStream_t s, const Params& p);
 void solve_iter_launch(size_t smem, cudaStream_t s, const Params& p, int mode);
 void solve_literal_launch(size_t smem, cudaStream_t s, const Params& p);
+size_t background_smem_bytes(int B, int BA);
+cudaError_t background_set_attributes(size_t smem);
+void background_launch(size_t smem, cudaStream_t s, const Params& p, double* mu, double* cov);
+}  // namespace mf
+
+#include <string>
+namespace mf {
+// message returned by mf_last_error() on the calling thread (defined in mf_api.cu)
+void set_last_error(const std::string& msg);
 
 }  // namespace mf

@@ -676,6 +676,59 @@ __global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p) {
   }
 }
 
+// Initial background statistics only (Fig. 1 initialisation): reduce the
+// statistics kernel's moments and write mu^0 and C^0 as float64 to caller
+// buffers mu_out (P, B) and cov_out (P, B, B).  N <= B gives NaN.
+__global__ void __launch_bounds__(kThreads) background_kernel(Params p, double* mu_out,
+                                                              double* cov_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int part = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int B = p.B, BA = p.BA;
+  const size_t pb = (size_t)part * B;
+  df* A = reinterpret_cast<df*>(smem_raw);
+  df* vm = A + (size_t)BA * BA;
+  df* vmu = vm + B;
+  df* vu3 = vmu + B;
+  df* vz0 = vu3 + B;
+  double* cov = cov_out + (size_t)part * B * B;
+  if (p.status[part] != MF_OK) {
+    for (int idx = tid; idx < B * B; idx += kThreads) cov[idx] = __longlong_as_double(0x7ff8000000000000LL);
+    for (int b = tid; b < B; b += kThreads) mu_out[pb + b] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
+  reduce_k1(p, part, A);
+  const df N = A[(B + 2) * BA + B + 2];
+  const bool enough = N.hi > (float)B;
+  const df invN = enough ? df_recip(N) : df{0.f, 0.f};
+  const df sa = A[B * BA + B + 2];
+  for (int b = tid; b < B; b += kThreads) {
+    const float m = p.pilot[pb + b];
+    vm[b] = df{m, 0.f};
+    const df mu = df_add(df{m, 0.f}, df_mul(df_fma(sa, df{m, 0.f}, A[b * BA + B + 2]), invN));
+    vmu[b] = mu;
+    vu3[b] = df_sub(df{m, 0.f}, mu);
+    vz0[b] = df{0.f, 0.f};
+  }
+  __syncthreads();
+  assemble(p, A, vm, vz0, vu3, invN, cov);
+  for (int b = tid; b < B; b += kThreads)
+    mu_out[pb + b] = enough ? df_to_double(vmu[b]) : __longlong_as_double(0x7ff8000000000000LL);
+  if (!enough)
+    for (int idx = tid; idx < B * B; idx += kThreads) cov[idx] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
+size_t background_smem_bytes(int B, int BA) {
+  return ((size_t)BA * BA + 4 * (size_t)B) * sizeof(df) + 64;
+}
+cudaError_t background_set_attributes(size_t smem) {
+  return cudaFuncSetAttribute(background_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+void background_launch(size_t smem, cudaStream_t s, const Params& p, double* mu, double* cov) {
+  background_kernel<<<p.P, kThreads, smem, s>>>(p, mu, cov);
+}
+
 cudaError_t solve_set_attributes(size_t s_init, size_t s_iter, size_t s_lit) {
   cudaError_t e = cudaFuncSetAttribute(solve_init_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_init);
