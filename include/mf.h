@@ -53,7 +53,12 @@ typedef enum {
 } mf_status;
 
 enum { MF_BIP = 0 };                       /* layout */
-enum { MF_FP32 = 0, MF_BF16SPLIT = 1 };    /* precision of the covariance accumulation */
+/* precision of the covariance accumulation:
+ *   MF_FP32       float32 products, double-float partial sums (SIMT)
+ *   MF_BF16SPLIT  every augmented pixel split into bf16 hi + lo and the
+ *                 moments H^T H + H^T L + L^T H accumulated in float32 on
+ *                 the tensor cores; supported for 64 <= B <= 92 */
+enum { MF_FP32 = 0, MF_BF16SPLIT = 1 };
 
 /* flags */
 #define MF_ALBEDO            1u  /* albedo factor r_i of Eq. (7); off: r_i = 1 (Fig. 1 caption) */

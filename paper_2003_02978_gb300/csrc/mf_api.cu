@@ -63,6 +63,7 @@ struct mf_plan_s {
   CUtensorMap map_stats{}, map_pixel{};
   cudaStream_t last_stream = nullptr;
   int device = 0;
+  int num_sms = 1;
   // host-I/O staging (mf_retrieve_host)
   float* h_cube = nullptr;
   uint8_t* h_mask = nullptr;
@@ -96,6 +97,8 @@ cudaError_t set_attrs(const mf_plan_s* pl) {
   const int bmax = mf::kMaxB;
   const int ba = (bmax + 3 + 3) / 4 * 4;
   cudaError_t e = mf::stats_set_attributes(pl->nj, mf::stats_smem_bytes(bmax_bucket));
+  if (e == cudaSuccess && pl->d.precision == MF_BF16SPLIT)
+    e = mf::stats_tc_set_attributes(pl->nj, pl->smem_stats);
   if (e == cudaSuccess) e = mf::pixel_set_attributes(pl->nj, mf::pixel_smem_bytes(bmax_bucket));
   if (e == cudaSuccess)
     e = mf::solve_set_attributes(mf::solve_init_smem_bytes(bmax, ba), mf::solve_iter_smem_bytes(bmax),
@@ -162,7 +165,13 @@ enum { KIND_STATS = 0, KIND_PIXEL = 1, KIND_SOLVE = 2, KIND_COUNT = 3 };
 
 void stats_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_STATS, s);
-  mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, pl->map_stats, prm, mode);
+  if (pl->d.precision == MF_BF16SPLIT) {
+    // persistent: one CTA per SM over the (column, chunk) work items
+    if (mode == mf::STAT_INIT) mf::pilot_launch(s, prm);
+    const int grid = std::min(pl->grid_stats, pl->num_sms);
+    mf::stats_tc_launch(pl->nj, grid, pl->smem_stats, s, pl->map_stats, prm, mode);
+  } else
+    mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, pl->map_stats, prm, mode);
   mark_end(m, s);
 }
 void pixel_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int acc, cudaStream_t s) {
@@ -218,8 +227,8 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
                 d->band_hi, (long long)d->bands_total);
   if (d->col_group < 1) return fail(MF_ERR_INVALID_ARG, "col_group must be >= 1");
   if (d->layout != MF_BIP) return fail(MF_ERR_UNSUPPORTED, "only the BIP layout is supported");
-  if (d->precision != MF_FP32)
-    return fail(MF_ERR_UNSUPPORTED, "precision %d not built in this library", d->precision);
+  if (d->precision != MF_FP32 && d->precision != MF_BF16SPLIT)
+    return fail(MF_ERR_INVALID_ARG, "unknown precision %d", d->precision);
   if (d->flags & ~(MF_ALBEDO | MF_SPARSE | MF_LITERAL | MF_PENALTY_NO_ALBEDO))
     return fail(MF_ERR_INVALID_ARG, "unknown flag bits 0x%x", d->flags);
   const int B = d->band_hi - d->band_lo;
@@ -230,6 +239,8 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
                 B, d->band_lo, (long long)d->bands_total, mf::kMaxB);
   if (d->rows > (1LL << 30) || d->cols > (1LL << 24) || d->rows * d->cols > (1LL << 40))
     return fail(MF_ERR_UNSUPPORTED, "cube too large");
+  if (d->precision == MF_BF16SPLIT && !mf::stats_tc_supported(B))
+    return fail(MF_ERR_UNSUPPORTED, "MF_BF16SPLIT supports windows of 64 to 92 bands, got %d", B);
 
   mf_plan_s* pl = new mf_plan_s();
   pl->d = *d;
@@ -259,13 +270,17 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
     const long target_ctas = 2400;
     long nsc = std::max<long>(1, (target_ctas + p.cols - 1) / p.cols);
     sc = (int)((p.rows + nsc - 1) / nsc);
+    // the tensor-core form accumulates a chunk in float32 in tensor memory:
+    // at most 1024 rows per chunk keeps that sum within the stated bound
+    if (d->precision == MF_BF16SPLIT) sc = std::min(sc, 1024);
   }
   sc = std::max(mf::kStatRows, (sc + mf::kStatRows - 1) / mf::kStatRows * mf::kStatRows);
   p.sc_rows = sc;
   p.n_sc = (p.rows + p.sc_rows - 1) / p.sc_rows;
   pl->grid_stats = p.cols * p.n_sc;
   pl->grid_pixel = p.n_ct * p.n_rb;
-  pl->smem_stats = mf::stats_smem_bytes(B);
+  pl->smem_stats = d->precision == MF_BF16SPLIT ? mf::stats_tc_smem_bytes(B)
+                                                 : mf::stats_smem_bytes(B);
   pl->smem_pixel = mf::pixel_smem_bytes(B);
   pl->smem_sinit = mf::solve_init_smem_bytes(B, p.BA);
   pl->smem_siter = mf::solve_iter_smem_bytes(B);
@@ -297,6 +312,8 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
   size_t total = 0;
   for (auto& pc : pieces) total = align_up(total, 256) + align_up(pc.bytes, 256);
   cudaError_t e = cudaGetDevice(&pl->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
   if (e == cudaSuccess) e = cudaMalloc(&pl->ws, total);
   if (e != cudaSuccess) {
     delete pl;

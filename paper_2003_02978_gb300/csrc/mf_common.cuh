@@ -127,6 +127,12 @@ void pixel_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorM
 void solve_init_launch(size_t smem, cudaStream_t s, const Params& p);
 void solve_iter_launch(size_t smem, cudaStream_t s, const Params& p, int mode);
 void solve_literal_launch(size_t smem, cudaStream_t s, const Params& p);
+size_t stats_tc_smem_bytes(int B);
+bool stats_tc_supported(int B);
+cudaError_t stats_tc_set_attributes(int nj, size_t smem);
+void stats_tc_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
+                     const Params& p, int mode);
+void pilot_launch(cudaStream_t s, const Params& p);
 size_t background_smem_bytes(int B, int BA);
 cudaError_t background_set_attributes(size_t smem);
 void background_launch(size_t smem, cudaStream_t s, const Params& p, double* mu, double* cov);

@@ -246,41 +246,6 @@ __device__ void chol_solve_df(const df* A, int n, int ld, const df* invd, df* x)
   __syncthreads();
 }
 
-// 3x3 solve with partial pivoting in double-float; returns det
-__device__ df solve3_df(df A[3][3], df b[3], df y[3]) {
-  df det{1.f, 0.f};
-  for (int col = 0; col < 3; ++col) {
-    int piv = col;
-    for (int r = col + 1; r < 3; ++r)
-      if (fabsf(A[r][col].hi) > fabsf(A[piv][col].hi)) piv = r;
-    if (piv != col) {
-      for (int k = 0; k < 3; ++k) {
-        const df t = A[col][k];
-        A[col][k] = A[piv][k];
-        A[piv][k] = t;
-      }
-      const df t = b[col];
-      b[col] = b[piv];
-      b[piv] = t;
-      det = df_neg(det);
-    }
-    det = df_mul(det, A[col][col]);
-    if (A[col][col].hi == 0.f) return df{0.f, 0.f};
-    const df inv = df_recip(A[col][col]);
-    for (int r = col + 1; r < 3; ++r) {
-      const df f = df_mul(A[r][col], inv);
-      for (int k = col; k < 3; ++k) A[r][k] = df_sub(A[r][k], df_mul(f, A[col][k]));
-      b[r] = df_sub(b[r], df_mul(f, b[col]));
-    }
-  }
-  for (int r = 2; r >= 0; --r) {
-    df s = b[r];
-    for (int k = r + 1; k < 3; ++k) s = df_sub(s, df_mul(A[r][k], y[k]));
-    y[r] = df_div(s, A[r][r]);
-  }
-  return det;
-}
-
 __device__ void fail_partition(const Params& p, int part, bool init) {
   const int B = p.B;
   const size_t pb = (size_t)part * B;
@@ -411,7 +376,6 @@ __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
 
 __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ df red[kWarps];
   __shared__ df s_y[3];
   __shared__ int s_bad;
   const int part = blockIdx.x;

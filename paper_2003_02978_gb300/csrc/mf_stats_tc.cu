@@ -1,0 +1,528 @@
+// Statistics kernel on the tensor cores (precision form MF_BF16SPLIT).
+//
+// Same quantity as the float32 statistics kernel: the augmented second
+// moments G = sum_i u_i u_i^T of u_i = [e_i, a_i, b_i, 1] (residual of the
+// albedo-direction split, Sec. II-C; see mf_stats.cu), per partition and
+// chunk of rows, which the solve kernels turn into C^0 (Fig. 1) or C^k
+// (Eq. (11), literal schedule).
+//
+// Each u_i (float32) is split into bf16 hi + lo (hi = bf16(u), lo =
+// bf16(u - hi)), so that u = hi + lo to about 2^-18 relative, and
+//   G = H^T H + H^T L + L^T H + L^T L.
+// (L^T L is small per product but biased on the diagonal; without it C^0
+// is off by ~1e-5 relative and alpha by ~2e-4.)  Since G is symmetric,
+// L^T H = (H^T L)^T, so two tcgen05.mma kind::f16 per 16 pixels suffice:
+//   D[:, 0 : 2 NP]  = H^T [H | L]       (M = 128, N = 2 NP)
+//   D[:, 0 : NP]   += L^T L             (M = 128, N = NP)
+// where NP = B + 4 rounded up to 16; an operand set holds H and L side by
+// side along N (MN-major core matrices), and an A operand is the first 128
+// columns from H's or L's start (the columns past NP are garbage rows of D
+// that the epilogue ignores).  D accumulates in float32 in tensor memory;
+// the epilogue forms Q = (H^T H + L^T L) / 2 + H^T L, and G = Q + Q^T is
+// completed where the per-item moments are summed (each moment entry is
+// stored as the pair (Q_ab, Q_ba), read as their sum).
+//
+// Persistent, warp-specialised kernel: one CTA per SM walks work items
+// (detector column, chunk of at most 1024 rows) with hand-offs on
+// shared-memory mbarriers only:
+//   warp 8 (producer): TMA box of 128 rows x B bands (float32) -> one of two
+//            float32 stages
+//   warps 0-7 (converters, a lane pair per pixel): albedo split,
+//            augmentation, bf16 hi/lo into MN-major core matrices of one of
+//            two operand sets
+//   warp 9 (issuer, one lane): 8 x 2 MMAs (K = 16 pixels each) per stage into
+//            one of two tensor-memory accumulators (alternating per item);
+//            tcgen05.commit frees the operand set / publishes the item
+//   warps 10-13 (epilogue): tcgen05.ld of a finished accumulator, moments of
+//            the item written as float pairs, accumulator released.
+// The reference direction of each partition (the mean of its first few
+// valid pixels, or mu^0) comes from global memory (pilot_kernel below for
+// the initialisation).
+#include "mf_common.cuh"
+#include "mf_pixel_io.cuh"
+#include "mf_tc.cuh"
+#include "mf_tma.cuh"
+#include "../../include/mf.h"
+
+#include <cuda_bf16.h>
+
+namespace mf {
+
+namespace {
+constexpr int kTcThreads = 448;     // 8 converter warps, producer, issuer, 4 epilogue warps
+constexpr int kTcConv = 256;        // converter threads (warps 0-7)
+constexpr int kTcRows = 128;          // pixels per stage (K of one stage)
+constexpr int kTcM = 128;             // MMA M (rows of G, >= B + 4)
+constexpr uint32_t kTmemCols = 512;   // two stage accumulators (2 NP each) and a running sum (NP)
+
+constexpr int kMaxFpStages = 3;
+
+struct TcSmem {
+  int NP;                  // N: augmented width rounded up to 16
+  int nfp;                 // float32 stages in flight (3, or 2 for wide windows)
+  size_t opb;              // one operand set: [H | L], 2 NP x 128 bf16
+  size_t kstride;          // bytes between core matrices along K (8 pixels)
+  size_t lo_off;           // L's first core matrix relative to H's
+  int accw;                // tensor-memory columns of one stage accumulator (2 NP, 32-aligned)
+  size_t stage_bytes;      // float32 stage: 128 rows x B
+  size_t ops_off, stage_off, ref_off, bar_off, slot_off, total;
+};
+__host__ __device__ inline TcSmem tc_layout_n(int B, int nfp) {
+  TcSmem L;
+  const int BA = (B + 6) / 4 * 4;
+  L.NP = (BA + 15) / 16 * 16;
+  L.nfp = nfp;
+  L.accw = (2 * L.NP + 31) / 32 * 32;  // accumulators at 0 and accw, running sum at 2 accw
+  L.lo_off = (size_t)(L.NP / 8) * 128;
+  L.kstride = 2 * L.lo_off;
+  L.opb = L.kstride * (kTcRows / 8);
+  L.stage_bytes = (size_t)kTcRows * B * sizeof(float);
+  // two operand sets, then the float32 stages: an A operand read from L's
+  // start in the last K group of set 1 runs 2048 - 16 NP bytes (NP >= 80)
+  // past the set, into the first stage, still inside the allocation
+  L.ops_off = 0;
+  L.stage_off = L.ops_off + 2 * L.opb;
+  L.ref_off = L.stage_off + nfp * L.stage_bytes;
+  L.bar_off = L.ref_off + 2 * (size_t)(kMaxB + 4) * sizeof(float);
+  L.slot_off = L.bar_off + 24 * sizeof(uint64_t);
+  L.total = L.slot_off + 16;
+  return L;
+}
+__host__ __device__ inline TcSmem tc_layout(int B) {
+  TcSmem L = tc_layout_n(B, kMaxFpStages);
+  if (L.total + 1024 > 227 * 1024) L = tc_layout_n(B, 2);
+  return L;
+}
+
+__device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
+  const __nv_bfloat162 lo2 = __floats2bfloat162_rn(a, b);
+  const __nv_bfloat162 hi2 = __floats2bfloat162_rn(c, d);
+  return make_uint2(*reinterpret_cast<const uint32_t*>(&lo2),
+                    *reinterpret_cast<const uint32_t*>(&hi2));
+}
+
+// write the bf16 hi and lo parts of 4 consecutive augmented entries
+// (n0 .. n0 + 3, n0 % 4 == 0) of pixel k into the MN-major operand buffers
+__device__ __forceinline__ void put4(unsigned char* H, unsigned char* Lo, size_t kstride, int n0,
+                                     int k, float4 v) {
+  const size_t off = (size_t)(k >> 3) * kstride + (size_t)(n0 >> 3) * 128 + (k & 7) * 16 +
+                     (n0 & 7) * 2;
+  const __nv_bfloat16 hx = __float2bfloat16_rn(v.x), hy = __float2bfloat16_rn(v.y);
+  const __nv_bfloat16 hz = __float2bfloat16_rn(v.z), hw = __float2bfloat16_rn(v.w);
+  const float rx = v.x - __bfloat162float(hx), ry = v.y - __bfloat162float(hy);
+  const float rz = v.z - __bfloat162float(hz), rw = v.w - __bfloat162float(hw);
+  *reinterpret_cast<uint2*>(H + off) =
+      pack_bf16x4(__bfloat162float(hx), __bfloat162float(hy), __bfloat162float(hz),
+                  __bfloat162float(hw));
+  *reinterpret_cast<uint2*>(Lo + off) = pack_bf16x4(rx, ry, rz, rw);
+}
+}  // namespace
+
+size_t stats_tc_smem_bytes(int B) { return tc_layout(B).total + 1024; }
+// 64 <= B <= 92.  B >= 64: with fewer bands the target is close to the albedo direction and
+// the 2^-18 representation error of the two-term split is amplified beyond
+// the stated bound (it also makes NP >= 80, so that an A operand, 128
+// columns from H's start, stays inside its K group, and one from L's start
+// ends inside the shared-memory allocation).  B <= 92: the two stage
+// accumulators and the running sum fit the 512 tensor-memory columns.
+bool stats_tc_supported(int B) {
+  if (B < 64 || B + 4 > kTcM || stats_tc_smem_bytes(B) > 227 * 1024) return false;
+  const TcSmem L = tc_layout(B);
+  return 2 * L.accw + L.NP <= (int)kTmemCols;  // B <= 92
+}
+
+// Mean of the first (up to) kPilot valid pixels of every partition
+// (row-major over its columns): the reference direction m of the initial
+// statistics.  Any m gives the same moments in exact arithmetic; a mean of a
+// few pixels rather than one leaves the augmented vectors [e, rho - 1, ..]
+// closer to zero mean, so that the float32 sums cancel less.  One warp per
+// partition.
+constexpr int kPilot = 8;
+__global__ void pilot_kernel(Params p) {
+  const int part = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (part >= p.P) return;
+  const int c0 = part * p.G, ncp = part_ncols(p, part);
+  const long total = (long)p.rows * ncp;
+  float sum[kMaxB / 32] = {};  // bands lane + 32 q
+  int n = 0;                   // warp-uniform
+  for (long base = 0; base < total && n < kPilot; base += 32) {
+    const long i = base + lane;
+    bool ok = false;
+    if (i < total) {
+      const int row = (int)(i / ncp), col = c0 + (int)(i % ncp);
+      ok = !p.mask || p.mask[(size_t)row * p.cols + col] == 0;
+      if (ok) {
+        const float4* px = reinterpret_cast<const float4*>(pixel_ptr(p, row, col));
+        for (int f = 0; f < p.B4; ++f) ok = ok && finite4(__ldg(px + f));
+      }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, ok);
+    while (bal && n < kPilot) {
+      const long v = base + __ffs(bal) - 1;
+      bal &= bal - 1;
+      const float* px = pixel_ptr(p, (int)(v / ncp), c0 + (int)(v % ncp));
+#pragma unroll
+      for (int q = 0; q < kMaxB / 32; ++q)
+        if (lane + 32 * q < p.B) sum[q] += px[lane + 32 * q];
+      ++n;
+    }
+  }
+  const float inv = n > 0 ? 1.f / (float)n : 0.f;
+#pragma unroll
+  for (int q = 0; q < kMaxB / 32; ++q)
+    if (lane + 32 * q < p.B) p.pilot[(size_t)part * p.B + lane + 32 * q] = sum[q] * inv;
+}
+
+// named barrier among the 8 converter warps
+__device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+template <int NJ>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    stats_tc_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int B = p.B, B4 = p.B4, BA = p.BA;
+  const TcSmem L = tc_layout(B);
+  const int NP = L.NP;
+  unsigned char* ops = smem_raw + L.ops_off;
+  const int NF = L.nfp;
+  float* stage_base = reinterpret_cast<float*>(smem_raw + L.stage_off);
+  auto stage = [&](int q) { return stage_base + (size_t)q * (L.stage_bytes / sizeof(float)); };
+  float* s_ref = reinterpret_cast<float*>(smem_raw + L.ref_off);  // [2][kMaxB + 4]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + L.bar_off);
+  uint64_t* fp_full = bars;        // [NF] float32 stage landed (TMA)
+  uint64_t* fp_empty = bars + 4;   // [NF] float32 stage read by every converter warp
+  uint64_t* op_full = bars + 8;    // [2] operand set written by every converter warp
+  uint64_t* op_empty = bars + 10;  // [2] MMAs reading the operand set completed
+  uint64_t* acc_full = bars + 12;  // [2] accumulator holds a finished item
+  uint64_t* acc_empty = bars + 14; // [2] accumulator drained by the epilogue warps
+  uint64_t* drain = bars + 16;     // abort path: every issued MMA completed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + L.slot_off);
+  const int nitems = p.cols * p.n_sc;
+  const uint32_t box_bytes = (uint32_t)(kTcRows * B * sizeof(float));
+
+  if (tid == 0) {
+    s_abort = 0;
+    for (int q = 0; q < NF; ++q) {
+      mbar_init(&fp_full[q], 1);
+      mbar_init(&fp_empty[q], kTcConv / 32);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&op_full[q], kTcConv / 32);
+      mbar_init(&op_empty[q], 1);
+      mbar_init(&acc_full[q], 1);
+      mbar_init(&acc_empty[q], 4);
+    }
+    mbar_init(drain, 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  auto item_geom = [&](int w, int& c, int& chunk, int& r_beg, int& r_end, int& nst) {
+    c = w % p.cols;
+    chunk = w / p.cols;
+    r_beg = chunk * p.sc_rows;
+    r_end = min(p.rows, r_beg + p.sc_rows);
+    nst = (r_end - r_beg + kTcRows - 1) / kTcRows;
+  };
+  bool failed = false;
+  int issued[kMaxFpStages] = {0, 0, 0};  // producer: copies per float32 stage
+
+  if (warp == 8) {
+    // ---------------- producer
+    if (lane == 0) {
+      prefetch_tmap(&map);
+      int g = 0;
+      for (int w = blockIdx.x; w < nitems && !failed; w += gridDim.x) {
+        int c, chunk, r_beg, r_end, nst;
+        item_geom(w, c, chunk, r_beg, r_end, nst);
+        for (int s = 0; s < nst; ++s, ++g) {
+          const int fb = g % NF;
+          if (!mbar_wait(&fp_empty[fb], (uint32_t)(((g / NF) & 1) ^ 1))) {
+            failed = true;
+            atomicExch(&s_abort, 1);
+            break;
+          }
+          mbar_arrive_expect_tx(&fp_full[fb], box_bytes);
+          tma_load_3d(stage(fb), &map, p.band_lo, c, r_beg + s * kTcRows, &fp_full[fb]);
+          ++issued[fb];
+        }
+      }
+    }
+  } else if (warp == 9) {
+    // ---------------- issuer
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc_bf16_mn(kTcM, 2 * NP);
+      const uint32_t idesc_ll = umma_idesc_bf16_mn(kTcM, NP);
+      const uint32_t ops_s = smem_u32(ops);
+      int g = 0;
+      for (int w = blockIdx.x; w < nitems && !failed; w += gridDim.x) {
+        int c, chunk, r_beg, r_end, nst;
+        item_geom(w, c, chunk, r_beg, r_end, nst);
+        for (int s = 0; s < nst; ++s, ++g) {
+          const int sb = g & 1;  // operand set and accumulator of this stage
+          if (!mbar_wait(&acc_empty[sb], (uint32_t)(((g >> 1) & 1) ^ 1)) ||
+              !mbar_wait(&op_full[sb], (uint32_t)((g >> 1) & 1))) {
+            failed = true;
+            atomicExch(&s_abort, 1);
+            break;
+          }
+          tc_fence_after();
+          const uint32_t acc = tmem + (uint32_t)(sb * L.accw);
+          const uint32_t os = ops_s + (uint32_t)(sb * L.opb);
+#pragma unroll 1
+          for (int kk = 0; kk < kTcRows / 16; ++kk) {
+            // A = 128 columns from H's (L's) start: H (L), then garbage
+            // rows of D; B = [H | L] (L)
+            const uint32_t ga = os + (uint32_t)(kk * 2 * L.kstride);
+            const uint64_t dh = umma_smem_desc(ga, (uint32_t)L.kstride, 128);
+            const uint64_t dl = umma_smem_desc(ga + (uint32_t)L.lo_off, (uint32_t)L.kstride, 128);
+            umma_bf16(acc, dh, dh, idesc, kk > 0 ? 1u : 0u);
+            umma_bf16(acc, dl, dl, idesc_ll, 1u);
+          }
+          umma_commit(&op_empty[sb]);
+          umma_commit(&acc_full[sb]);
+        }
+      }
+    }
+  } else if (warp >= 10) {
+    // ---------------- epilogue: stage accumulator -> running sum -> moments
+    // Each stage's D (128 pixels, 16 MMAs) is added in float32 into the
+    // item's running sum Q, kept in tensor memory: short accumulation
+    // chains on the tensor cores, one rounded add per stage here.
+    const int quad = warp & 3;            // a warp may access TMEM lanes 32 (warp % 4) ..
+    const int m = quad * 32 + lane;       // row of G
+    const int K1E = k1_entries(BA);
+    const int nb = BA / 4;
+    const int bi = m >> 2, u = m & 3;
+    // index of block (r, r) in the packed upper-triangular block list
+    auto blk_diag = [&](int r) { return r * nb - (r * (r - 1)) / 2; };
+    const int blk_row = blk_diag(bi);
+    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+    const uint32_t qsum = tmem + lanes + (uint32_t)(2 * L.accw);
+    int g = 0;
+    for (int w = blockIdx.x; w < nitems && !failed; w += gridDim.x) {
+      int c, chunk, r_beg, r_end, nst;
+      item_geom(w, c, chunk, r_beg, r_end, nst);
+      const int part = part_of(p, c);
+      const int unit = (c - part * p.G) * p.n_sc + chunk;
+      // entry (a, b) of G = Q_ab + Q_ba: row m of Q gives the first term of
+      // the entries (m, j >= m's block) and the second of (j, m)
+      float* dst = reinterpret_cast<float*>(p.k1part + ((size_t)part * p.G * p.n_sc + unit) * K1E);
+      for (int s = 0; s < nst; ++s, ++g) {
+        const int sb = g & 1;
+        // warp-uniform decision: tcgen05.ld below needs every lane
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[sb], (uint32_t)((g >> 1) & 1)))) {
+          failed = true;
+          atomicExch(&s_abort, 1);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + lanes + (uint32_t)(sb * L.accw);
+        const bool last = s == nst - 1;
+        for (int c0 = 0; c0 < NP; c0 += 8) {
+          uint32_t hh[8], hl[8], qs[8];
+          tmem_ld8(acc + (uint32_t)c0, hh);
+          tmem_ld8(acc + (uint32_t)(NP + c0), hl);
+          if (s > 0) tmem_ld8(qsum + (uint32_t)c0, qs);
+          tmem_wait_ld();
+          // Q = (H^T H + L^T L) / 2 + H^T L  (+ the running sum)
+          float q[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            q[k] = fmaf(0.5f, __uint_as_float(hh[k]), __uint_as_float(hl[k]));
+            if (s > 0) q[k] += __uint_as_float(qs[k]);
+          }
+          if (!last) {
+            tmem_st8(qsum + (uint32_t)c0, q);
+          } else if (m < BA) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int j = c0 + k;
+              const int bj = j >> 2, v = j & 3;
+              if (j >= BA) continue;
+              if (bj >= bi) dst[2 * ((blk_row + (bj - bi)) * 16 + u * 4 + v)] = q[k];
+              if (bj <= bi) dst[2 * ((blk_diag(bj) + (bi - bj)) * 16 + v * 4 + u) + 1] = q[k];
+            }
+          }
+        }
+        if (!last) tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[sb]);
+      }
+    }
+  } else {
+    // ---------------- converters (warps 0-7)
+    const int e = lane & 1;
+    const int slot = warp * 16 + (lane >> 1);  // pixel = K index within a stage
+    const bool albedo = (p.flags & MF_ALBEDO) != 0;
+    // (item, stage) after (w, s) in this CTA's sequence, for the prefetch
+    auto next_of = [&](int& w, int& s) {
+      int c, chunk, r_beg, r_end, nst;
+      item_geom(w, c, chunk, r_beg, r_end, nst);
+      if (++s >= nst) {
+        s = 0;
+        w += gridDim.x;
+      }
+    };
+    auto fetch = [&](int w, int s, int& m_out, float& a_out) {
+      m_out = 0;
+      a_out = 0.f;
+      if (w >= nitems) return;
+      int c, chunk, r_beg, r_end, nst;
+      item_geom(w, c, chunk, r_beg, r_end, nst);
+      const int row = r_beg + s * kTcRows + slot;
+      if (row < r_end) {
+        const size_t pix = (size_t)row * p.cols + c;
+        if (p.mask) m_out = p.mask[pix];
+        if (mode == STAT_LITERAL) a_out = p.alpha[pix];
+      }
+    };
+    int pw = blockIdx.x, ps = 0;
+    int m_nx;
+    float a_nx;
+    fetch(pw, ps, m_nx, a_nx);
+    int g = 0, t = 0;
+    // reference direction of an item's partition, double-buffered by item:
+    // the next item's is loaded into registers during the current item and
+    // published by the named barrier that ends it
+    const float* refsrc = (mode == STAT_INIT ? p.pilot : p.mu0f);
+    auto ref_of = [&](int w) -> float {
+      if (w >= nitems || tid >= B) return 0.f;
+      return refsrc[(size_t)part_of(p, w % p.cols) * B + tid];
+    };
+    if (tid < B) s_ref[tid] = ref_of(blockIdx.x);
+    conv_bar();
+    // every converter warp walks every item (and reaches every named barrier)
+    // even after a failed wait; it only skips the work
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x, ++t) {
+      int c, chunk, r_beg, r_end, nst;
+      item_geom(w, c, chunk, r_beg, r_end, nst);
+      const int part = part_of(p, c);
+      float* ref = s_ref + (t & 1) * (kMaxB + 4);
+      const float ref_next = ref_of(w + gridDim.x);
+      float inv_ref2;
+      if (mode == STAT_INIT) {
+        float n2 = 0.f;
+        for (int b = lane; b < B; b += 32) n2 = fmaf(ref[b], ref[b], n2);
+        n2 = warp_sumf(n2);
+        inv_ref2 = n2 > 0.f ? 1.f / n2 : 0.f;
+      } else {
+        inv_ref2 = p.pscal[(size_t)part * PS_N + PS_INVMU2];
+      }
+      const float4* ref4 = reinterpret_cast<const float4*>(ref);
+      for (int s = 0; s < nst; ++s, ++g) {
+        const int m_cur = m_nx;
+        const float a_cur = a_nx;
+        next_of(pw, ps);
+        fetch(pw, ps, m_nx, a_nx);
+        if (__any_sync(0xffffffffu, failed || *(volatile int*)&s_abort)) {
+          failed = true;
+          continue;
+        }
+        const int fb = g % NF, sb = g & 1;
+        const int row = r_beg + s * kTcRows + slot;
+        const bool inb = row < r_end;
+        // warp-uniform decision: the shuffles below need every lane
+        const bool ok_w = mbar_wait(&fp_full[fb], (uint32_t)((g / NF) & 1)) &&
+                          mbar_wait(&op_empty[sb], (uint32_t)(((g >> 1) & 1) ^ 1));
+        if (!__all_sync(0xffffffffu, ok_w)) {
+          failed = true;
+          atomicExch(&s_abort, 1);
+          continue;
+        }
+        unsigned char* H = ops + (size_t)sb * L.opb;
+        unsigned char* Lo = H + L.lo_off;
+        const float* px = stage(fb) + (size_t)slot * B;
+        float4 x[NJ];
+        const bool fin = lds_pixel<NJ>(px, inb, e, B4, x);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&fp_empty[fb]);
+        const bool valid = inb && fin && m_cur == 0;
+        const float rho = pair_dot<NJ>(x, ref4, e, B4) * inv_ref2;
+        split_residual<NJ>(x, ref4, rho, e, B4);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int f = e + 2 * j;
+          if (f < B4) put4(H, Lo, L.kstride, 4 * f, slot, valid ? x[j] : make_float4(0.f, 0.f, 0.f, 0.f));
+        }
+        if (e == 0) {
+          float bcf = 0.f;
+          if (mode == STAT_LITERAL && valid) {
+            const float r = albedo ? rho : 1.f;
+            bcf = r > 0.f ? -(r * a_cur) : 0.f;
+          }
+          put4(H, Lo, L.kstride, B, slot,
+               valid ? make_float4(rho - 1.f, bcf, 1.f, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f));
+          for (int n0 = BA; n0 < NP; n0 += 4)
+            put4(H, Lo, L.kstride, n0, slot, make_float4(0.f, 0.f, 0.f, 0.f));
+        }
+        fence_proxy_async_smem();  // operand writes -> tensor core (async proxy)
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&op_full[sb]);
+      }
+      if (tid < B) s_ref[((t + 1) & 1) * (kMaxB + 4) + tid] = ref_next;
+      conv_bar();
+    }
+  }
+  if (failed) atomicExch(&s_abort, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (s_abort) {
+    // bounded waits for this CTA's copies and MMAs still in flight, then
+    // release the tensor memory
+    if (warp == 8 && lane == 0)
+      for (int q = 0; q < NF; ++q)
+        if (issued[q] > 0) mbar_wait(&fp_full[q], (uint32_t)((issued[q] - 1) & 1));
+    if (warp == 9 && lane == 0) {
+      umma_commit(drain);
+      mbar_wait(drain, 0);
+    }
+    if (tid == 0)
+      for (int w = blockIdx.x; w < nitems; w += gridDim.x) p.status[part_of(p, w % p.cols)] = MF_ERR_TIMEOUT;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+#define MF_NJ_CASES(X) X(8) X(9) X(10) X(12)
+
+cudaError_t stats_tc_set_attributes(int nj, size_t smem) {
+#define MF_CASE(NJ)                                                                    \
+  case NJ:                                                                             \
+    return cudaFuncSetAttribute(stats_tc_kernel<NJ>,                                   \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  switch (nj) { MF_NJ_CASES(MF_CASE) }
+#undef MF_CASE
+  return cudaErrorInvalidValue;
+}
+
+void pilot_launch(cudaStream_t s, const Params& p) {
+  pilot_kernel<<<(p.P + 3) / 4, 128, 0, s>>>(p);
+}
+
+void stats_tc_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
+                     const Params& p, int mode) {
+#define MF_CASE(NJ)                                                           \
+  case NJ:                                                                    \
+    stats_tc_kernel<NJ><<<grid, kTcThreads, smem, s>>>(map, p, mode);         \
+    return;
+  switch (nj) { MF_NJ_CASES(MF_CASE) }
+#undef MF_CASE
+}
+
+}  // namespace mf

@@ -52,7 +52,9 @@ def _desc(**kw):
 @pytest.mark.parametrize("kw,code", [
     (dict(rows=0), 1), (dict(cols=-1), 1), (dict(band_lo=10, band_hi=8), 1),
     (dict(band_hi=80), 1), (dict(col_group=0), 1), (dict(layout=3), 8),
-    (dict(precision=7), 8), (dict(flags=1 << 9), 1), (dict(band_lo=2, band_hi=74, bands_total=80), 8),
+    (dict(precision=7), 1), (dict(precision=1, bands_total=128, band_hi=128), 8),
+    (dict(precision=1, bands_total=32, band_hi=32), 8), (dict(precision=1, band_lo=12), 8),
+    (dict(flags=1 << 9), 1), (dict(band_lo=2, band_hi=74, bands_total=80), 8),
     (dict(band_lo=0, band_hi=6), 8), (dict(bands_total=200, band_hi=200), 8),
 ])
 def test_descriptor_validation(lib, kw, code):

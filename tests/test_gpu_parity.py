@@ -25,14 +25,14 @@ def built():
 
 
 def gpu_retrieve(cube_np, k, lam, eps, n_iter, mask=None, flags=ALBEDO | SPARSE, col_group=1,
-                 band_lo=0, band_hi=None, alpha_init=None, albedo=False):
+                 band_lo=0, band_hi=None, alpha_init=None, albedo=False, precision=0):
     import paper_2003_02978_gb300 as mfg
     rows, cols, bt = cube_np.shape
     cube = torch.from_numpy(np.ascontiguousarray(cube_np, dtype=np.float32)).cuda()
     m = None if mask is None else torch.from_numpy(np.ascontiguousarray(mask, np.uint8)).cuda()
     ai = None if alpha_init is None else torch.from_numpy(
         np.ascontiguousarray(alpha_init, np.float32)).cuda()
-    plan = mfg.Plan(rows, cols, bt, band_lo, band_hi, col_group, flags)
+    plan = mfg.Plan(rows, cols, bt, band_lo, band_hi, col_group, flags, precision)
     alb = torch.empty((rows, cols), dtype=torch.float32, device="cuda") if albedo else None
     a = plan.retrieve(cube, np.asarray(k, np.float32), lam, eps, n_iter, mask=m, alpha_init=ai,
                       albedo=alb)
@@ -45,14 +45,14 @@ def gpu_retrieve(cube_np, k, lam, eps, n_iter, mask=None, flags=ALBEDO | SPARSE,
 
 
 def compare(cube_np, k, lam, eps, n_iter, mask=None, flags=ALBEDO | SPARSE, col_group=1,
-            band_lo=0, band_hi=None, alpha_init=None, tol=TOL_FP32):
+            band_lo=0, band_hi=None, alpha_init=None, tol=TOL_FP32, precision=0):
     kk = f32(k)
     ref, st_ref = oracle.retrieve(cube_np.astype(np.float64), kk, lam, eps, n_iter, mask=mask,
                                   band_lo=band_lo, band_hi=band_hi, col_group=col_group,
                                   flags=flags,
                                   alpha_init=None if alpha_init is None else f32(alpha_init))
     got, st = gpu_retrieve(cube_np, k, lam, eps, n_iter, mask, flags, col_group, band_lo,
-                           band_hi, alpha_init)
+                           band_hi, alpha_init, precision=precision)
     np.testing.assert_array_equal(st, st_ref)
     win = cube_np[:, :, band_lo:band_hi]
     valid = oracle.valid_pixels(win, mask)
@@ -213,3 +213,88 @@ def test_flightline_full_size_sampled_columns(flags):
     amp = oracle.retrieve_amplification(sub.astype(np.float64), f32(sc.k), prm["lam"], prm["eps"],
                                         prm["n_iter"], mask=msk)
     check_alpha(got[:, cols], ref, valid, amp)
+
+
+# ------------------------------------------------- BF16-split tensor-core form
+BF16SPLIT = 1
+# stated bound of the BF16-split form (hi + lo bf16 products on the tensor
+# cores, float32 accumulation): the same 1e-4 bar as float32
+TOL_BF16SPLIT = 1e-4
+
+
+@pytest.mark.parametrize("n_iter", [0, 1, 10])
+def test_bf16split_small_workload(n_iter):
+    sc, prm = workload_scene("plain-512x16x72", seed=0)
+    compare(sc.cube.numpy(), sc.k, prm["lam"], prm["eps"], n_iter, precision=BF16SPLIT,
+            tol=TOL_BF16SPLIT)
+
+
+def test_bf16split_literal():
+    sc, prm = workload_scene("plain-512x16x72", seed=3)
+    compare(sc.cube.numpy(), sc.k, prm["lam"], prm["eps"], 5, flags=ALBEDO | SPARSE | LITERAL,
+            precision=BF16SPLIT, tol=TOL_BF16SPLIT)
+
+
+@pytest.mark.parametrize("rows,cols,bt,G,lo,hi,tol", [
+    (517, 13, 72, 1, 0, None, TOL_BF16SPLIT), (1000, 9, 64, 1, 0, None, TOL_BF16SPLIT),
+    (700, 10, 80, 5, 0, None, TOL_BF16SPLIT), (400, 8, 84, 1, 4, 76, TOL_BF16SPLIT),
+    (900, 5, 88, 1, 0, None, TOL_BF16SPLIT), (2600, 3, 72, 1, 0, None, TOL_BF16SPLIT),
+    (600, 6, 92, 1, 0, None, TOL_BF16SPLIT), (300, 7, 120, 1, 16, 108, TOL_BF16SPLIT),
+    (1100, 4, 68, 2, 0, None, TOL_BF16SPLIT)])
+def test_bf16split_ragged(rows, cols, bt, G, lo, hi, tol):
+    sc = make_scene(rows, cols, bt, n_plumes=2, plume_sigma=(3.0, 6.0),
+                    plume_peak=(800.0, 3000.0), mask_frac=0.03, seed=rows + 3 * cols)
+    compare(sc.cube.numpy(), sc.k[lo:hi if hi else bt], 1e-3, 1e-9, 6, mask=sc.mask.numpy(),
+            col_group=G, band_lo=lo, band_hi=hi, precision=BF16SPLIT, tol=tol)
+
+
+@pytest.mark.parametrize("bands", [8, 16, 32, 60, 96, 112, 128])
+def test_bf16split_rejects_unsupported_windows(bands):
+    """With few bands the target is nearly parallel to the albedo direction
+    and the 2^-18 representation error of the two-term bf16 split is
+    amplified past the bound (8 bands: alpha^0 error 4.7e-4 emulated; 16
+    bands: e_2 9.3e-3 measured): the form takes windows of at least 64 bands,
+    and at most 92 (two stage accumulators of 2 NP columns and a running sum
+    of NP columns in 512 tensor-memory columns).  The plan is refused with
+    MF_ERR_UNSUPPORTED."""
+    import paper_2003_02978_gb300 as mfg
+    with pytest.raises(mfg.MFError) as ei:
+        mfg.Plan(300, 4, bands, precision=BF16SPLIT)
+    assert ei.value.status == 8
+
+
+def test_bf16split_background_error():
+    """C^0 and mu^0 of the tensor-core form against the FP64 oracle."""
+    import paper_2003_02978_gb300 as mfg
+    sc, prm = workload_scene("plain-512x16x72", seed=10)
+    cube = sc.cube.numpy()
+    plan = mfg.Plan(512, 16, 72, precision=BF16SPLIT)
+    plan.retrieve(sc.cube.cuda(), sc.k, prm["lam"], prm["eps"], 0)
+    mu, cov = plan.background()
+    mu, cov = mu.cpu().numpy(), cov.cpu().numpy()
+    for c in range(16):
+        X = cube[:, c].astype(np.float64)
+        m = X.mean(0)
+        C = (X - m).T @ (X - m) / len(X)
+        np.testing.assert_allclose(mu[c], m, rtol=1e-6)
+        assert np.linalg.norm(cov[c] - C) / np.linalg.norm(C) < 1e-5
+
+
+def test_bf16split_flightline_sampled():
+    import paper_2003_02978_gb300 as mfg
+    sc, prm = workload_scene("flightline-4000x598x72", seed=0, device="cuda")
+    plan = mfg.Plan(4000, 598, 72, precision=BF16SPLIT)
+    a = plan.retrieve(sc.cube, sc.k, prm["lam"], prm["eps"], prm["n_iter"], mask=sc.mask)
+    torch.cuda.synchronize()
+    assert np.all(plan.status() == 0)
+    got = a.cpu().numpy()
+    cols = np.unique(np.concatenate([np.random.default_rng(2).choice(598, 8, replace=False),
+                                     [0, 597]]))
+    sub = sc.cube[:, cols, :].cpu().numpy()
+    msk = sc.mask[:, cols].cpu().numpy()
+    ref, st = oracle.retrieve(sub.astype(np.float64), f32(sc.k), prm["lam"], prm["eps"],
+                              prm["n_iter"], mask=msk)
+    valid = oracle.valid_pixels(sub, msk)
+    amp = oracle.retrieve_amplification(sub.astype(np.float64), f32(sc.k), prm["lam"],
+                                        prm["eps"], prm["n_iter"], mask=msk)
+    check_alpha(got[:, cols], ref, valid, amp, TOL_BF16SPLIT)
