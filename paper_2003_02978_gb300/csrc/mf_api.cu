@@ -257,14 +257,28 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
   p.flags = d->flags;
   pl->nj = nj_bucket(p.B4);
 
+  cudaError_t e = cudaGetDevice(&pl->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
+  if (e != cudaSuccess) {
+    delete pl;
+    return fail(MF_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
+  }
   // row blocking: pixel kernel blocks of rb rows (a multiple of the stage
-  // height); statistics chunks sized so that the statistics grid has several
-  // CTAs per SM
-  int rb = std::max(mf::kStageRows, env_int("MF_RB_ROWS", 256));
+  // height), as few as fill the SMs once (column tiles x row blocks ~ the
+  // resident pixel CTAs per SM x SM count); statistics chunks sized so that the
+  // statistics grid has several CTAs per SM
+  p.n_ct = (p.cols + mf::kTileCols - 1) / mf::kTileCols;
+  int rb = env_int("MF_RB_ROWS", 0);
+  if (rb <= 0) {
+    const long waves = (long)mf::pixel_ctas_per_sm(pl->nj) * pl->num_sms;
+    const long nrb = std::max<long>(1, (waves + p.n_ct - 1) / p.n_ct);
+    rb = (int)((p.rows + nrb - 1) / nrb);
+  }
+  rb = std::max(rb, mf::kStageRows);
   rb = (rb + mf::kStageRows - 1) / mf::kStageRows * mf::kStageRows;
   p.rb_rows = std::min(rb, (p.rows + mf::kStageRows - 1) / mf::kStageRows * mf::kStageRows);
   p.n_rb = (p.rows + p.rb_rows - 1) / p.rb_rows;
-  p.n_ct = (p.cols + mf::kTileCols - 1) / mf::kTileCols;
   int sc = env_int("MF_SC_ROWS", 0);
   if (sc <= 0) {
     const long target_ctas = 2400;
@@ -311,10 +325,7 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
   };
   size_t total = 0;
   for (auto& pc : pieces) total = align_up(total, 256) + align_up(pc.bytes, 256);
-  cudaError_t e = cudaGetDevice(&pl->device);
-  if (e == cudaSuccess)
-    e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
-  if (e == cudaSuccess) e = cudaMalloc(&pl->ws, total);
+  e = cudaMalloc(&pl->ws, total);
   if (e != cudaSuccess) {
     delete pl;
     if (e == cudaErrorMemoryAllocation)

@@ -28,9 +28,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxB = 128;
 constexpr int kTileCols = 16;     // pixel kernel: adjacent columns per tile (one lane pair each)
-constexpr int kStageRows = 8;     // pixel kernel: rows per pipeline stage (one per warp)
+constexpr int kStageRows = 8;     // pixel kernel: rows per pipeline stage (one per consumer warp)
 constexpr int kStatRows = 128;    // statistics kernel: rows per pipeline stage
-constexpr int kPixStages = 2;
 
 enum : int { PS_Q = 0, PS_MUV, PS_COFF, PS_INVMU2, PS_N };
 enum : int { DS_N = 0, DS_BBAR, DS_Q, DS_N2 };
@@ -114,6 +113,7 @@ __host__ __device__ inline void block_of(int t, int nb, int& bi, int& bj) {
 // (each defined in the translation unit that defines the kernel)
 size_t stats_smem_bytes(int B);
 size_t pixel_smem_bytes(int B);
+int pixel_ctas_per_sm(int nj);  // resident pixel CTAs per SM for a template bucket
 size_t solve_init_smem_bytes(int B, int BA);
 size_t solve_iter_smem_bytes(int B);
 size_t solve_literal_smem_bytes(int B, int BA);

@@ -14,11 +14,15 @@
 // with v = (C^k)^{-1} t(mu^k) and q = t^T v prepared by the solve kernel.
 //
 // Layout: a CTA owns a tile of 16 adjacent detector columns over a block of
-// rows.  Each pipeline stage is one TMA box of 8 rows x 16 columns x B bands
-// (contiguous 16 x B x 4 bytes per row in HBM), double buffered on
-// mbarriers; warp w consumes row w of a stage, lane pair s column s, so every
-// lane pair keeps the same column (partition) and its moments in registers.
-// alpha and the mask of the next stage are prefetched into registers.
+// rows; the plan sizes the row blocks so that the grid is one wave of two
+// CTAs per SM (one for windows over 72 bands).  Each pipeline stage is one TMA box of 8 rows x 16 columns x
+// B bands (contiguous 16 x B x 4 bytes per row in HBM), double buffered on
+// full / empty mbarriers; warp w takes row w of every stage, lane pair s
+// column s, so that every lane pair keeps the same column (partition) and
+// its moments in registers.  The band arithmetic is packed two-wide
+// (fma.rn.f32x2); alpha and the mask of the next stage are prefetched into
+// registers; thread 0 refills the buffer of the previous stage at the start
+// of each stage.
 #include "mf_common.cuh"
 #include "mf_pixel_io.cuh"
 #include "mf_tma.cuh"
@@ -27,6 +31,9 @@
 namespace mf {
 
 namespace {
+constexpr int kPixThreads = kStageRows * 32;  // one warp per stage row
+constexpr int kPixStages = 2;
+
 struct PixSmem {
   size_t stage_bytes, bar_off, par_off, total;
 };
@@ -41,10 +48,15 @@ __host__ __device__ inline PixSmem pix_layout(int B) {
 }
 }  // namespace
 
+// two CTAs per SM (registers capped at 128 per thread) up to 72 bands; one
+// above, where the band registers would spill
+constexpr int pix_ctas_per_sm(int nj) { return nj <= 9 ? 2 : 1; }
+
 size_t pixel_smem_bytes(int B) { return pix_layout(B).total + 128; }
+int pixel_ctas_per_sm(int nj) { return pix_ctas_per_sm(nj); }
 
 template <int NJ>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     pixel_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode, int accumulate) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_abort;
@@ -70,25 +82,26 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < kPixStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kWarps);
+    for (int q = 0; q < kPixStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kStageRows);
     }
     mbar_fence_init();
   }
   __syncthreads();
-  int issued[kPixStages] = {0};  // copies issued per stage buffer (thread 0)
+  int issued[kPixStages] = {0};  // thread 0: copies issued per stage buffer
+  auto load = [&](int q, int i) {
+    mbar_arrive_expect_tx(&full[q], box_bytes);
+    tma_load_3d(smem_raw + q * L.stage_bytes, &map, p.band_lo, c0t, r_beg + i * kStageRows,
+                &full[q]);
+    ++issued[q];
+  };
   if (tid == 0) {
     prefetch_tmap(&map);
-    for (int s = 0; s < kPixStages && s < nst; ++s) {
-      mbar_arrive_expect_tx(&full[s], box_bytes);
-      tma_load_3d(smem_raw + s * L.stage_bytes, &map, p.band_lo, c0t, r_beg + s * kStageRows,
-                  &full[s]);
-      ++issued[s];
-    }
+    for (int i = 0; i < kPixStages && i < nst; ++i) load(i, i);
   }
   // per-column parameters of the current pass
-  for (int idx = tid; idx < kTileCols * B; idx += kThreads) {
+  for (int idx = tid; idx < kTileCols * B; idx += kPixThreads) {
     const int cc = idx / B, b = idx % B;
     float m = 0.f, v = 0.f;
     if (cc < nc) {
@@ -113,14 +126,15 @@ __global__ void __launch_bounds__(kThreads, 2)
   __syncthreads();
 
   const int e = lane & 1;
-  const int s_col = lane >> 1;          // column within the tile
+  const int s_col = lane >> 1;  // column within the tile
   const bool col_ok = s_col < nc;
   const int c = c0t + s_col;
   const float4 sc = reinterpret_cast<const float4*>(s_sc)[s_col];
   const float q = sc.x, muv = sc.y, coff = sc.z, invmu2 = sc.w;
   const bool failed = s_failed[s_col] != 0;
-  const float4* mu4 = reinterpret_cast<const float4*>(s_mu + s_col * B);
-  const float4* v4 = reinterpret_cast<const float4*>(s_v + s_col * B);
+  const bool any_failed = __any_sync(0xffffffffu, failed);
+  const float* mu_s = s_mu + s_col * B;
+  const float* v_s = s_v + s_col * B;
   const bool albedo = (p.flags & MF_ALBEDO) != 0;
   const bool sparse = (p.flags & MF_SPARSE) != 0;
   const bool pna = (p.flags & MF_PENALTY_NO_ALBEDO) != 0;
@@ -128,12 +142,12 @@ __global__ void __launch_bounds__(kThreads, 2)
   const bool iter = mode == PIX_ITER;
   const float* ain = iter ? p.alpha : p.alpha_init;
 
-  float g[NJ][4];
+  float4 g[NJ];  // sum beta_i e_i over the lane's band groups
 #pragma unroll
-  for (int j = 0; j < NJ; ++j) g[j][0] = g[j][1] = g[j][2] = g[j][3] = 0.f;
+  for (int j = 0; j < NJ; ++j) g[j] = make_float4(0.f, 0.f, 0.f, 0.f);
   float sb = 0.f, sb2 = 0.f, sba = 0.f;
 
-  // prefetch alpha (previous estimate or alpha_init) and the mask of stage 0
+  // alpha (previous estimate or alpha_init) and the mask of stage i
   auto fetch = [&](int i, float& a_out, int& m_out) {
     const int row = r_beg + i * kStageRows + warp;
     a_out = 0.f;
@@ -147,28 +161,53 @@ __global__ void __launch_bounds__(kThreads, 2)
   float a_nx;
   int m_nx;
   fetch(0, a_nx, m_nx);
-
   for (int i = 0; i < nst; ++i) {
-    const int sb_ = i % kPixStages;
+    const int sq = i % kPixStages;
+    // refill the previous stage's buffer once every warp has read it
+    if (tid == 0 && i >= 1 && i - 1 + kPixStages < nst) {
+      const int qr = (i - 1) % kPixStages;
+      if (mbar_wait(&empty[qr], (uint32_t)(((i - 1) / kPixStages) & 1)))
+        load(qr, i - 1 + kPixStages);
+      else
+        atomicExch(&s_abort, 1);
+    }
     const float a_cur = a_nx;
     const int m_cur = m_nx;
     fetch(i + 1, a_nx, m_nx);
-    if (!mbar_wait(&full[sb_], (uint32_t)((i / kPixStages) & 1))) {
+    // warp-uniform decision: the pair shuffles below need every lane
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[sq], (uint32_t)((i / kPixStages) & 1)))) {
       atomicExch(&s_abort, 1);
       break;
     }
     const int row = r_beg + i * kStageRows + warp;
     const bool inb = row < r_end && col_ok;
-    const float* px = reinterpret_cast<const float*>(smem_raw + sb_ * L.stage_bytes) +
+    const float* px = reinterpret_cast<const float*>(smem_raw + sq * L.stage_bytes) +
                       (size_t)(warp * kTileCols + s_col) * B;
     float4 x[NJ];
-    const bool fin = lds_pixel<NJ>(px, inb, e, B4, x);
+    lds_groups_raw<NJ>(px, inb, e, B4, x);
+    // a pixel of an excluded partition is NaN when finite, 0 otherwise: an
+    // exact per-element test there (its mu0 need not be finite)
+    bool fin_exact = true;
+    if (any_failed) {
+      bool f = true;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) f = f && finite4(x[j]);
+      fin_exact = __shfl_xor_sync(0xffffffffu, (int)f, 1) && f;
+    }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[sb_]);
+    if (lane == 0) mbar_arrive(&empty[sq]);
+
+    float4 ref[NJ];
+    lds_groups<NJ>(mu_s, e, B4, ref);
+    const float rho_raw = pair_dot2<NJ>(x, ref);
+    const float rho = rho_raw * invmu2;
+    split_residual2<NJ>(x, ref, rho);
+    lds_groups<NJ>(v_s, e, B4, ref);
+    const float pe = pair_dot2<NJ>(x, ref);
+
+    // every band finite <=> the dot with the (finite) mu0 is finite
+    const bool fin = failed ? fin_exact : isfinite(rho_raw);
     const bool valid = inb && fin && m_cur == 0;
-    const float rho = pair_dot<NJ>(x, mu4, e, B4) * invmu2;
-    split_residual<NJ>(x, mu4, rho, e, B4);
-    const float pe = pair_dot<NJ>(x, v4, e, B4);
     const float pp = pe + (rho - 1.f) * muv - coff;
     const float r = albedo ? rho : 1.f;
     float al;
@@ -191,59 +230,42 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (!iter && p.albedo) p.albedo[pix] = valid ? r : 0.f;
     }
     if (accumulate) {
+      // excluded pixels may hold non-finite bands: they add nothing
       const bool use = valid && !failed && r > 0.f;
       const float beta = use ? r * al : 0.f;
-      if (!use) {  // excluded pixels may hold non-finite bands: 0 * NaN is NaN
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
       if (e == 0) {
         sb += beta;
         sb2 = fmaf(beta, beta, sb2);
         sba = fmaf(beta, use ? rho - 1.f : 0.f, sba);
       }
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        g[j][0] = fmaf(beta, x[j].x, g[j][0]);
-        g[j][1] = fmaf(beta, x[j].y, g[j][1]);
-        g[j][2] = fmaf(beta, x[j].z, g[j][2]);
-        g[j][3] = fmaf(beta, x[j].w, g[j][3]);
-      }
-    }
-    // refill this stage once every warp has read it
-    if (tid == 0 && i + kPixStages < nst) {
-      if (!mbar_wait(&empty[sb_], (uint32_t)((i / kPixStages) & 1))) {
-        atomicExch(&s_abort, 1);
-      } else {
-        mbar_arrive_expect_tx(&full[sb_], box_bytes);
-        tma_load_3d(smem_raw + sb_ * L.stage_bytes, &map, p.band_lo, c0t,
-                    r_beg + (i + kPixStages) * kStageRows, &full[sb_]);
-        ++issued[sb_];
-      }
+      if (use) axpy2<NJ>(g, beta, x);
     }
   }
   __syncthreads();
   if (s_abort) {
     if (tid == 0) {
       // bounded wait for the last copy issued on each buffer before the CTA exits
-      for (int s = 0; s < kPixStages; ++s)
-        if (issued[s] > 0) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1));
+      for (int q2 = 0; q2 < kPixStages; ++q2)
+        if (issued[q2] > 0) mbar_wait(&full[q2], (uint32_t)((issued[q2] - 1) & 1));
       for (int cc = 0; cc < nc; ++cc) p.status[part_of(p, c0t + cc)] = MF_ERR_TIMEOUT;
     }
     return;
   }
   if (!accumulate) return;
 
-  // ---- moments of the tile, per column: sum over the 8 warps (fixed order)
+  // ---- moments of the tile, per column: sum over the 8 warps (fixed
+  // order); every copy has landed and been read, so the stages are free
   const int E3 = B + 3;
-  float* red = reinterpret_cast<float*>(smem_raw);  // [kWarps][kTileCols][E3]
+  float* red = reinterpret_cast<float*>(smem_raw);  // [kStageRows][kTileCols][E3]
   float* mine = red + ((size_t)warp * kTileCols + s_col) * E3;
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     const int f = e + 2 * j;
     if (f < B4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) mine[3 + 4 * f + u] = g[j][u];
+      mine[3 + 4 * f] = g[j].x;  // offset 3: scalar stores (not 16-byte aligned)
+      mine[4 + 4 * f] = g[j].y;
+      mine[5 + 4 * f] = g[j].z;
+      mine[6 + 4 * f] = g[j].w;
     }
   }
   if (e == 0) {
@@ -253,15 +275,15 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   __syncthreads();
   const int K3E = k3_entries(B);
-  for (int t = tid; t < nc * E3; t += kThreads) {
+  for (int t = tid; t < nc * E3; t += kPixThreads) {
     const int cc = t / E3, j = t % E3;
-    float s = 0.f;
+    float sum = 0.f;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += red[((size_t)w * kTileCols + cc) * E3 + j];
+    for (int w = 0; w < kStageRows; ++w) sum += red[((size_t)w * kTileCols + cc) * E3 + j];
     const int col = c0t + cc;
     const int part = part_of(p, col);
     const int unit = (col - part * p.G) * p.n_rb + rb;
-    p.k3part[((size_t)part * p.G * p.n_rb + unit) * K3E + j] = s;
+    p.k3part[((size_t)part * p.G * p.n_rb + unit) * K3E + j] = sum;
   }
 }
 
@@ -281,7 +303,7 @@ void pixel_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorM
                   const Params& p, int mode, int accumulate) {
 #define MF_CASE(NJ)                                                        \
   case NJ:                                                                 \
-    pixel_kernel<NJ><<<grid, kThreads, smem, s>>>(map, p, mode, accumulate); \
+    pixel_kernel<NJ><<<grid, kPixThreads, smem, s>>>(map, p, mode, accumulate); \
     return;
   switch (nj) { MF_NJ_CASES(MF_CASE) }
 #undef MF_CASE

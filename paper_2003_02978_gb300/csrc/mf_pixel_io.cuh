@@ -82,4 +82,67 @@ __device__ __forceinline__ void split_residual(float4 (&x)[NJ], const float4* re
   }
 }
 
+// load the lane's float4 groups of one pixel from shared memory, without a
+// finiteness test (groups past B4, or a pixel out of range, read as zero)
+template <int NJ>
+__device__ __forceinline__ void lds_groups_raw(const float* px, bool inb, int e, int B4,
+                                               float4 (&x)[NJ]) {
+  const float4* p4 = reinterpret_cast<const float4*>(px);
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int f = e + 2 * j;
+    x[j] = (inb && f < B4) ? p4[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+// register-resident reference vector: r[j] holds the lane's group f = e + 2 j
+// (zero where f >= B4)
+template <int NJ>
+__device__ __forceinline__ void lds_groups(const float* v, int e, int B4, float4 (&r)[NJ]) {
+  lds_groups_raw<NJ>(v, true, e, B4, r);
+}
+
+// Packed two-lane float32 arithmetic (fma.rn.f32x2): each instruction does
+// the .xy or .zw half of a float4 group, correctly rounded per element.
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+
+// dot over the pair's bands (two packed partial sums per lane, then the
+// pair's shuffle).  Any non-finite element of x makes the result non-finite
+// (x * 0 is NaN for x = +-Inf or NaN), so the caller's finiteness test of
+// the dot replaces a per-element test, for every finite ref.
+template <int NJ>
+__device__ __forceinline__ float pair_dot2(const float4 (&x)[NJ], const float4 (&ref)[NJ]) {
+  float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    d0 = __ffma2_rn(lo2(x[j]), lo2(ref[j]), d0);
+    d1 = __ffma2_rn(hi2(x[j]), hi2(ref[j]), d1);
+  }
+  const float d = (d0.x + d0.y) + (d1.x + d1.y);
+  return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+// x <- x - rho * ref
+template <int NJ>
+__device__ __forceinline__ void split_residual2(float4 (&x)[NJ], const float4 (&ref)[NJ],
+                                                float rho) {
+  const float2 m = make_float2(-rho, -rho);
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const float2 a = __ffma2_rn(m, lo2(ref[j]), lo2(x[j]));
+    const float2 b = __ffma2_rn(m, hi2(ref[j]), hi2(x[j]));
+    x[j] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+// acc <- acc + s * x
+template <int NJ>
+__device__ __forceinline__ void axpy2(float4 (&acc)[NJ], float s, const float4 (&x)[NJ]) {
+  const float2 m = make_float2(s, s);
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const float2 a = __ffma2_rn(m, lo2(x[j]), lo2(acc[j]));
+    const float2 b = __ffma2_rn(m, hi2(x[j]), hi2(acc[j]));
+    acc[j] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
 }  // namespace mf
