@@ -99,7 +99,8 @@ cudaError_t set_attrs(const mf_plan_s* pl) {
   cudaError_t e = mf::stats_set_attributes(pl->nj, mf::stats_smem_bytes(bmax_bucket));
   if (e == cudaSuccess && pl->d.precision == MF_BF16SPLIT)
     e = mf::stats_tc_set_attributes(pl->nj, pl->smem_stats);
-  if (e == cudaSuccess) e = mf::pixel_set_attributes(pl->nj, mf::pixel_smem_bytes(bmax_bucket));
+  if (e == cudaSuccess)
+    e = mf::pixel_set_attributes(pl->nj, mf::pixel_smem_bytes(bmax_bucket, pl->nj));
   if (e == cudaSuccess)
     e = mf::solve_set_attributes(mf::solve_init_smem_bytes(bmax, ba), mf::solve_iter_smem_bytes(bmax),
                                  mf::solve_literal_smem_bytes(bmax, ba));
@@ -295,7 +296,7 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
   pl->grid_pixel = p.n_ct * p.n_rb;
   pl->smem_stats = d->precision == MF_BF16SPLIT ? mf::stats_tc_smem_bytes(B)
                                                  : mf::stats_smem_bytes(B);
-  pl->smem_pixel = mf::pixel_smem_bytes(B);
+  pl->smem_pixel = mf::pixel_smem_bytes(B, pl->nj);
   pl->smem_sinit = mf::solve_init_smem_bytes(B, p.BA);
   pl->smem_siter = mf::solve_iter_smem_bytes(B);
   pl->smem_slit = mf::solve_literal_smem_bytes(B, p.BA);

@@ -112,7 +112,7 @@ __host__ __device__ inline void block_of(int t, int nb, int& bi, int& bj) {
 // ------------------------------------------------------- host-side launchers
 // (each defined in the translation unit that defines the kernel)
 size_t stats_smem_bytes(int B);
-size_t pixel_smem_bytes(int B);
+size_t pixel_smem_bytes(int B, int nj);
 int pixel_ctas_per_sm(int nj);  // resident pixel CTAs per SM for a template bucket
 size_t solve_init_smem_bytes(int B, int BA);
 size_t solve_iter_smem_bytes(int B);

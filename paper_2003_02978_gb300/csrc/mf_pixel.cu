@@ -37,13 +37,15 @@ constexpr int kPixStages = 2;
 struct PixSmem {
   size_t stage_bytes, bar_off, par_off, total;
 };
-__host__ __device__ inline PixSmem pix_layout(int B) {
+// BP = 8 NJ >= B: per-column parameter stride, zero-padded so that a lane's
+// band groups e + 2 j (j < NJ) load without a bounds test
+__host__ __device__ inline PixSmem pix_layout(int B, int BP) {
   PixSmem L;
   L.stage_bytes = (size_t)kStageRows * kTileCols * B * sizeof(float);
   L.bar_off = kPixStages * L.stage_bytes;
   L.par_off = L.bar_off + 2 * kPixStages * sizeof(uint64_t);
-  // per column: mu0f[B], v[B], 4 scalars
-  L.total = L.par_off + (size_t)kTileCols * (2 * B + 4) * sizeof(float);
+  // per column: mu0f[BP], v[BP], 4 scalars
+  L.total = L.par_off + (size_t)kTileCols * (2 * BP + 4) * sizeof(float);
   return L;
 }
 }  // namespace
@@ -52,7 +54,7 @@ __host__ __device__ inline PixSmem pix_layout(int B) {
 // above, where the band registers would spill
 constexpr int pix_ctas_per_sm(int nj) { return nj <= 9 ? 2 : 1; }
 
-size_t pixel_smem_bytes(int B) { return pix_layout(B).total + 128; }
+size_t pixel_smem_bytes(int B, int nj) { return pix_layout(B, 8 * nj).total + 128; }
 int pixel_ctas_per_sm(int nj) { return pix_ctas_per_sm(nj); }
 
 template <int NJ>
@@ -68,12 +70,13 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
   const int nc = min(kTileCols, p.cols - c0t);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int B = p.B, B4 = p.B4;
-  const PixSmem L = pix_layout(B);
+  constexpr int BP = 8 * NJ;
+  const PixSmem L = pix_layout(B, BP);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bar_off);
   uint64_t* empty = full + kPixStages;
   float* s_mu = reinterpret_cast<float*>(smem_raw + L.par_off);
-  float* s_v = s_mu + kTileCols * B;
-  float* s_sc = s_v + kTileCols * B;
+  float* s_v = s_mu + kTileCols * BP;
+  float* s_sc = s_v + kTileCols * BP;
 
   const int r_beg = rb * p.rb_rows;
   const int r_end = min(p.rows, r_beg + p.rb_rows);
@@ -101,10 +104,10 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     for (int i = 0; i < kPixStages && i < nst; ++i) load(i, i);
   }
   // per-column parameters of the current pass
-  for (int idx = tid; idx < kTileCols * B; idx += kPixThreads) {
-    const int cc = idx / B, b = idx % B;
+  for (int idx = tid; idx < kTileCols * BP; idx += kPixThreads) {
+    const int cc = idx / BP, b = idx % BP;
     float m = 0.f, v = 0.f;
-    if (cc < nc) {
+    if (cc < nc && b < B) {
       const size_t pb = (size_t)part_of(p, c0t + cc) * B + b;
       m = p.mu0f[pb];
       v = p.vf[pb];
@@ -133,8 +136,14 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
   const float q = sc.x, muv = sc.y, coff = sc.z, invmu2 = sc.w;
   const bool failed = s_failed[s_col] != 0;
   const bool any_failed = __any_sync(0xffffffffu, failed);
-  const float* mu_s = s_mu + s_col * B;
-  const float* v_s = s_v + s_col * B;
+  const float4* mu_s = reinterpret_cast<const float4*>(s_mu + s_col * BP) + e;
+  const float4* v_s = reinterpret_cast<const float4*>(s_v + s_col * BP) + e;
+  // the lane's band groups e + 2 j of a stage pixel; past the window (odd
+  // B4, or a template bucket wider than B) the last group is read again:
+  // mu0 and v are zero there, and those groups of the moments are dropped
+  int goff[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) goff[j] = min(e + 2 * j, B4 - 1);
   const bool albedo = (p.flags & MF_ALBEDO) != 0;
   const bool sparse = (p.flags & MF_SPARSE) != 0;
   const bool pna = (p.flags & MF_PENALTY_NO_ALBEDO) != 0;
@@ -184,7 +193,8 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     const float* px = reinterpret_cast<const float*>(smem_raw + sq * L.stage_bytes) +
                       (size_t)(warp * kTileCols + s_col) * B;
     float4 x[NJ];
-    lds_groups_raw<NJ>(px, inb, e, B4, x);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) x[j] = reinterpret_cast<const float4*>(px)[goff[j]];
     // a pixel of an excluded partition is NaN when finite, 0 otherwise: an
     // exact per-element test there (its mu0 need not be finite)
     bool fin_exact = true;
@@ -198,11 +208,13 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     if (lane == 0) mbar_arrive(&empty[sq]);
 
     float4 ref[NJ];
-    lds_groups<NJ>(mu_s, e, B4, ref);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) ref[j] = mu_s[2 * j];
     const float rho_raw = pair_dot2<NJ>(x, ref);
     const float rho = rho_raw * invmu2;
     split_residual2<NJ>(x, ref, rho);
-    lds_groups<NJ>(v_s, e, B4, ref);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) ref[j] = v_s[2 * j];
     const float pe = pair_dot2<NJ>(x, ref);
 
     // every band finite <=> the dot with the (finite) mu0 is finite

@@ -82,25 +82,6 @@ __device__ __forceinline__ void split_residual(float4 (&x)[NJ], const float4* re
   }
 }
 
-// load the lane's float4 groups of one pixel from shared memory, without a
-// finiteness test (groups past B4, or a pixel out of range, read as zero)
-template <int NJ>
-__device__ __forceinline__ void lds_groups_raw(const float* px, bool inb, int e, int B4,
-                                               float4 (&x)[NJ]) {
-  const float4* p4 = reinterpret_cast<const float4*>(px);
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    const int f = e + 2 * j;
-    x[j] = (inb && f < B4) ? p4[f] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-// register-resident reference vector: r[j] holds the lane's group f = e + 2 j
-// (zero where f >= B4)
-template <int NJ>
-__device__ __forceinline__ void lds_groups(const float* v, int e, int B4, float4 (&r)[NJ]) {
-  lds_groups_raw<NJ>(v, true, e, B4, r);
-}
-
 // Packed two-lane float32 arithmetic (fma.rn.f32x2): each instruction does
 // the .xy or .zw half of a float4 group, correctly rounded per element.
 __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
