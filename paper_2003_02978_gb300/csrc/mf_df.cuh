@@ -100,4 +100,66 @@ __device__ __forceinline__ float df_to_float(df x) { return __fadd_rn(x.hi, x.lo
 
 __device__ __forceinline__ bool df_isfinite(df x) { return isfinite(x.hi) && isfinite(x.lo); }
 
+// A double-float matrix in shared memory stored as two float planes (hi at
+// h[i * ld + j], lo one plane further), so that adjacent elements of a row
+// load as float2 pairs for the packed arithmetic below.  ld is even.
+struct DfMat {
+  float* h;
+  int ld;
+  int plane;  // float offset of the lo plane
+  __device__ __forceinline__ df get(int i, int j) const {
+    return df{h[i * ld + j], h[plane + i * ld + j]};
+  }
+  __device__ __forceinline__ void set(int i, int j, df v) const {
+    h[i * ld + j] = v.hi;
+    h[plane + i * ld + j] = v.lo;
+  }
+  // elements (i, j) and (i, j + 1), j even
+  __device__ __forceinline__ float2 hi2(int i, int j) const {
+    return *reinterpret_cast<const float2*>(h + i * ld + j);
+  }
+  __device__ __forceinline__ float2 lo2(int i, int j) const {
+    return *reinterpret_cast<const float2*>(h + plane + i * ld + j);
+  }
+  __device__ __forceinline__ void set2(int i, int j, float2 hi, float2 lo) const {
+    *reinterpret_cast<float2*>(h + i * ld + j) = hi;
+    *reinterpret_cast<float2*>(h + plane + i * ld + j) = lo;
+  }
+};
+
+// Packed pairs of double-floats (hi and lo as float2), on the fma.rn.f32x2 /
+// add.rn.f32x2 / mul.rn.f32x2 instructions: the same error-free
+// transformations per element as above.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, exact negation
+}
+// c - w * a for a packed pair a (hi ah, lo al) and one double-float w given
+// as (w.hi, -w.hi, w.lo): the product's error terms are formed exactly, its
+// sum with c by TwoSum of the high parts and a plain float sum of the low
+// parts (error <= about 2^-47 (|c| + |w a|), the bound the factorisations'
+// backward error analysis uses).
+__device__ __forceinline__ void df2_fnma(float2& ch, float2& cl, float wh, float wnh, float wl,
+                                         float2 ah, float2 al) {
+  const float2 pn = __fmul2_rn(f2(wnh), ah);            // -p, p = fl(w.hi * a.hi)
+  float2 pe = __ffma2_rn(f2(wh), ah, pn);               // w.hi * a.hi - p (exact)
+  pe = __ffma2_rn(f2(wh), al, pe);
+  pe = __ffma2_rn(f2(wl), ah, pe);                      // w a = p + pe
+  const float2 s = __fadd2_rn(ch, pn);                  // TwoSum(c.hi, -p)
+  const float2 bb = sub2(s, ch);
+  const float2 e = __fadd2_rn(sub2(ch, sub2(s, bb)), sub2(pn, bb));
+  const float2 lo = __fadd2_rn(e, sub2(cl, pe));
+  ch = __fadd2_rn(s, lo);                               // Fast2Sum
+  cl = sub2(lo, sub2(ch, s));
+}
+// packed double-float product by one double-float w: (ah, al) * w
+__device__ __forceinline__ void df2_mul1(float2& ah, float2& al, df w) {
+  const float2 p = __fmul2_rn(ah, f2(w.hi));
+  float2 e = __ffma2_rn(ah, f2(w.hi), __fmul2_rn(p, f2(-1.f)));
+  e = __ffma2_rn(ah, f2(w.lo), e);
+  e = __ffma2_rn(al, f2(w.hi), e);
+  ah = __fadd2_rn(p, e);
+  al = sub2(e, sub2(ah, p));
+}
+
 }  // namespace mf

@@ -95,153 +95,218 @@ __device__ df block_dot_df(const df* a, const df* b, int n, df* red) {
   return block_sum_df(d.result(), red);
 }
 
+// block t of the packed upper-triangular list of nb x nb blocks -> (bi, bj):
+// row r starts at r nb - r (r - 1) / 2 (closed form, corrected by one)
+__device__ __forceinline__ void block_rc(int t, int nb, int& bi, int& bj) {
+  const float b2 = 2.f * nb + 1.f;
+  int r = (int)((b2 - sqrtf(b2 * b2 - 8.f * (float)t)) * 0.5f);
+  auto start = [&](int x) { return x * nb - (x * (x - 1)) / 2; };
+  if (r < 0) r = 0;
+  if (r > nb - 1) r = nb - 1;
+  if (start(r) > t) --r;
+  else if (r + 1 < nb && start(r + 1) <= t) ++r;
+  bi = r;
+  bj = r + (t - start(r));
+}
+
 // reduce the per-CTA augmented moments of `part` into the full symmetric
-// BA x BA matrix A (shared memory)
-__device__ void reduce_k1(const Params& p, int part, df* A) {
+// BA x BA matrix A; each thread keeps 2 x 8 loads in flight
+__device__ void reduce_k1(const Params& p, int part, const DfMat& A) {
   const int BA = p.BA, K1E = k1_entries(BA), nb = BA / 4;
   const int nunits = part_ncols(p, part) * p.n_sc;
   const float2* P0 = p.k1part + (size_t)part * p.G * p.n_sc * K1E;
-  for (int q = threadIdx.x; q < K1E; q += kThreads) {
-    df s{0.f, 0.f};
-    for (int u = 0; u < nunits; ++u) s = df_add(s, ldf(P0, (size_t)u * K1E + q));
-    int bi, bj;
-    block_of(q >> 4, nb, bi, bj);
-    const int w = q & 15;
-    const int i = 4 * bi + (w >> 2), j = 4 * bj + (w & 3);
-    A[i * BA + j] = s;
-    A[j * BA + i] = s;
-  }
-  __syncthreads();
-}
-
-// C = (1/N) sum (e + a u1 + b u2 + u3)(...)^T from the augmented moments,
-// written into the lower triangle (diagonal included) of A's leading B x B
-// block; the border rows/columns B.. of A are read, not written.
-__device__ void assemble(const Params& p, df* A, const df* u1, const df* u2, const df* u3, df invN,
-                         double* S_out) {
-  const int B = p.B, BA = p.BA;
-  const df aa = A[B * BA + B], ab = A[B * BA + B + 1], bb = A[(B + 1) * BA + B + 1];
-  const df a1 = A[B * BA + B + 2], b1 = A[(B + 1) * BA + B + 2], n1 = A[(B + 2) * BA + B + 2];
-  const int cnt = B * (B + 1) / 2;
-  for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
-    int i = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-    while (i * (i + 1) / 2 > idx) --i;
-    while ((i + 1) * (i + 2) / 2 <= idx) ++i;
-    const int j = idx - i * (i + 1) / 2;
-    df v = A[i * BA + j];
-    v = df_fma(A[i * BA + B], u1[j], v);
-    v = df_fma(u1[i], A[j * BA + B], v);
-    v = df_fma(A[i * BA + B + 1], u2[j], v);
-    v = df_fma(u2[i], A[j * BA + B + 1], v);
-    v = df_fma(A[i * BA + B + 2], u3[j], v);
-    v = df_fma(u3[i], A[j * BA + B + 2], v);
-    v = df_fma(aa, df_mul(u1[i], u1[j]), v);
-    v = df_fma(ab, df_add(df_mul(u1[i], u2[j]), df_mul(u2[i], u1[j])), v);
-    v = df_fma(bb, df_mul(u2[i], u2[j]), v);
-    v = df_fma(a1, df_add(df_mul(u1[i], u3[j]), df_mul(u3[i], u1[j])), v);
-    v = df_fma(b1, df_add(df_mul(u2[i], u3[j]), df_mul(u3[i], u2[j])), v);
-    v = df_fma(n1, df_mul(u3[i], u3[j]), v);
-    v = df_mul(v, invN);
-    A[i * BA + j] = v;
-    if (S_out) {
-      const double d = df_to_double(v);
-      S_out[(size_t)i * B + j] = d;
-      S_out[(size_t)j * B + i] = d;
+  constexpr int kU = 8;
+  for (int q0 = threadIdx.x; q0 < K1E; q0 += 2 * kThreads) {
+    df sum[2] = {df{0.f, 0.f}, df{0.f, 0.f}};
+    for (int u0 = 0; u0 < nunits; u0 += kU) {
+      float2 v[2][kU];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+          const int q = q0 + h * kThreads, u = u0 + k;
+          v[h][k] = (q < K1E && u < nunits) ? P0[(size_t)u * K1E + q] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k = 0; k < kU; ++k) sum[h] = df_add(sum[h], df{v[h][k].x, v[h][k].y});
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = q0 + h * kThreads;
+      if (q >= K1E) continue;
+      int bi, bj;
+      block_rc(q >> 4, nb, bi, bj);
+      const int w = q & 15;
+      const int i = 4 * bi + (w >> 2), j = 4 * bj + (w & 3);
+      A.set(i, j, sum[h]);
+      A.set(j, i, sum[h]);
     }
   }
   __syncthreads();
 }
 
-// In-place Cholesky of the lower triangle of the leading n x n block (row
-// stride ld): right-looking, one column per step and one barrier per step.
-// Step j reads the pivot d = A_jj (final since step j-1), updates the
-// trailing block with the unscaled column j times 1/d, and scales column
-// j-1 by its 1/L (column j-1 is no longer read).  invd[j] = 1/L_jj; the
-// diagonal of L is written after the loop (no step reads it).  Returns false
-// (uniformly) if a pivot is not > 0.
-__device__ bool cholesky_df(df* A, int n, int ld, df* invd, int* flag) {
-  const int tid = threadIdx.x;
-  (void)flag;
-  bool ok = true;
+// C = (1/N) sum (e + a u1 + b u2 + u3)(...)^T from the augmented moments
+// G (symmetric in A), written into the upper triangle (diagonal included)
+// of A's leading B x B block; the border rows B.. of A are read, not
+// written.  With P_i, R_i, Q_i the coefficients of u1_j, u2_j, u3_j,
+//   C_ij N = G_ij + u1_j P_i + u2_j R_i + u3_j Q_i
+//          + u1_i G_ja + u2_i G_jb + u3_i G_j1,
+//   P_i = G_ia + G_aa u1_i + G_ab u2_i + G_a1 u3_i   (R_i, Q_i likewise),
+// the same sum of terms as expanding the outer product.  u2 == nullptr
+// means u2 = 0 (the initial statistics).  scratch: 3 B double-floats.
+__device__ void assemble(const Params& p, const DfMat& A, const df* u1, const df* u2, const df* u3,
+                         df invN, double* S_out, df* scratch) {
+  const int B = p.B;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const df zero{0.f, 0.f};
+  auto Ga = [&](int i) { return A.get(B, i); };
+  auto Gb = [&](int i) { return A.get(B + 1, i); };
+  auto G1 = [&](int i) { return A.get(B + 2, i); };
+  const df aa = Ga(B), ab = Ga(B + 1), a1 = Ga(B + 2);
+  const df bb = Gb(B + 1), b1 = Gb(B + 2), n1 = G1(B + 2);
+  df* P = scratch;
+  df* R = P + B;
+  df* Q = R + B;
+  for (int i = tid; i < B; i += kThreads) {
+    df pa = df_fma(a1, u3[i], df_fma(aa, u1[i], Ga(i)));
+    df q1 = df_fma(n1, u3[i], df_fma(a1, u1[i], G1(i)));
+    df rb = zero;
+    if (u2) {
+      pa = df_fma(ab, u2[i], pa);
+      q1 = df_fma(b1, u2[i], q1);
+      rb = df_fma(b1, u3[i], df_fma(bb, u2[i], df_fma(ab, u1[i], Gb(i))));
+    }
+    P[i] = pa;
+    R[i] = rb;
+    Q[i] = q1;
+  }
+  __syncthreads();
+  for (int j = warp; j < B; j += kWarps) {
+    const df u1j = u1[j], u3j = u3[j], Gaj = Ga(j), G1j = G1(j);
+    const df u2j = u2 ? u2[j] : zero, Gbj = Gb(j);
+    for (int i = j + lane; i < B; i += 32) {
+      df v = A.get(j, i);  // G_ji = G_ij
+      v = df_fma(u1j, P[i], v);
+      v = df_fma(u3j, Q[i], v);
+      v = df_fma(u1[i], Gaj, v);
+      v = df_fma(u3[i], G1j, v);
+      if (u2) {
+        v = df_fma(u2j, R[i], v);
+        v = df_fma(u2[i], Gbj, v);
+      }
+      v = df_mul(v, invN);
+      A.set(j, i, v);
+      if (S_out) {
+        const double d = df_to_double(v);
+        S_out[(size_t)i * B + j] = d;
+        S_out[(size_t)j * B + i] = d;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// In-place Cholesky C = U^T U of the upper triangle (diagonal included) of
+// the leading n x n block (n even); the strict lower triangle is not
+// referenced (it may be overwritten).  Right-looking, one row per step and
+// one barrier per step: step j reads the pivot d = A_jj (final since step
+// j-1) and the unscaled row j, updates rows i > j as
+// A_ik -= (A_ji / d) A_jk (k >= i; warps take rows, lanes the contiguous k
+// in packed pairs), and scales row j-1 by its 1/U (row j-1 is no longer
+// read).  invd[j] = 1/U_jj; U's diagonal is written after the loop.
+// Returns false (uniformly: every thread reads the same pivot) if a pivot
+// is not > 0.
+__device__ bool cholesky_upper_df(const DfMat& A, int n, df* invd) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    const df d = A[j * ld + j];
-    if (!(d.hi > 0.f) || !df_isfinite(d)) {
-      ok = false;  // uniform: every thread reads the same pivot
-      break;
-    }
-    const df r = df_rsqrt(d);        // 1/sqrt(d), same in every thread
-    const df rinv = df_mul(r, r);    // 1/d
+    const df d = A.get(j, j);
+    if (!(d.hi > 0.f) || !df_isfinite(d)) return false;
+    const df r = df_rsqrt(d);      // 1/sqrt(d), same in every thread
+    const df rinv = df_mul(r, r);  // 1/d
     if (j > 0) {
       const df rp = invd[j - 1];
-      for (int i = j + tid; i < n; i += kThreads) A[i * ld + j - 1] = df_mul(A[i * ld + j - 1], rp);
+      for (int k = j + tid; k < n; k += kThreads) A.set(j - 1, k, df_mul(A.get(j - 1, k), rp));
     }
-    const int m = n - j - 1;
-    const int cnt = m * (m + 1) / 2;
-    for (int idx = tid; idx < cnt; idx += kThreads) {
-      int ii = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-      while (ii * (ii + 1) / 2 > idx) --ii;
-      while ((ii + 1) * (ii + 2) / 2 <= idx) ++ii;
-      const int kk = idx - ii * (ii + 1) / 2;
-      const int i = j + 1 + ii, k = j + 1 + kk;
-      A[i * ld + k] = df_sub(A[i * ld + k], df_mul(df_mul(A[i * ld + j], A[k * ld + j]), rinv));
+    for (int i = j + 1 + warp; i < n; i += kWarps) {
+      const df w = df_mul(A.get(j, i), rinv);
+      // pairs (k, k + 1) from the even k <= i; k = i - 1 lies in the
+      // unreferenced lower triangle
+      for (int k = (i & ~1) + 2 * lane; k < n; k += 64) {
+        float2 ch = A.hi2(i, k), cl = A.lo2(i, k);
+        df2_fnma(ch, cl, w.hi, -w.hi, w.lo, A.hi2(j, k), A.lo2(j, k));
+        A.set2(i, k, ch, cl);
+      }
     }
     if (tid == 0) invd[j] = r;
     __syncthreads();
   }
-  if (!ok) return false;
-  for (int j = tid; j < n; j += kThreads) A[j * ld + j] = df_recip(invd[j]);
+  for (int j = tid; j < n; j += kThreads) A.set(j, j, df_recip(invd[j]));
   __syncthreads();
   return true;
 }
 
-// X = L^{-1} stored transposed in the strict upper triangle of A
-// (A[j][i] = X[i][j], j < i); X's diagonal is invd.  Right-looking row
-// elimination of L X = I, one barrier per step: step i updates the rows
-// below with the still unscaled row i times 1/L_ii, and scales row i-1
-// (no longer read).
-__device__ void tri_inverse_df(df* A, int n, int ld, const df* invd) {
-  const int tid = threadIdx.x;
+// X = L^{-1}, L = U^T (U from cholesky_upper_df, upper triangle of A), into
+// the strict lower triangle of A (A[r][j] = X[r][j], j < r); X's diagonal
+// is invd.  Right-looking elimination of L X = I with unscaled rows R
+// (X[i][.] = R[i][.] / L_ii): step i updates the rows r > i as
+// R[r][j] -= (L_ri / L_ii) R[i][j], j <= i (R[i][i] = 1; warps take rows,
+// lanes the contiguous j in packed pairs), one barrier per step; the rows
+// are scaled after the loop.
+__device__ void tri_inverse_df(const DfMat& A, int n, const df* invd) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int idx = tid; idx < n * n; idx += kThreads) {
-    const int j = idx / n, i = idx % n;
-    if (j < i) A[j * ld + i] = df{0.f, 0.f};
+    const int r = idx / n, j = idx % n;
+    if (j < r) A.set(r, j, df{0.f, 0.f});
   }
   __syncthreads();
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i + 1 < n; ++i) {
     const df di = invd[i];
-    if (i > 0) {
-      const df dp = invd[i - 1];
-      for (int j = tid; j < i - 1; j += kThreads) A[j * ld + i - 1] = df_mul(A[j * ld + i - 1], dp);
-    }
-    const int rows = n - i - 1, cols = i + 1;
-    for (int idx = tid; idx < rows * cols; idx += kThreads) {
-      const int r = i + 1 + idx / cols, j = idx % cols;
-      // X[i][j] = invd_i * R[i][j] (j < i), X[i][i] = invd_i
-      const df xij = (j == i) ? di : df_mul(A[j * ld + i], di);
-      A[j * ld + r] = df_sub(A[j * ld + r], df_mul(A[r * ld + i], xij));
+    for (int r = i + 1 + warp; r < n; r += kWarps) {
+      const df w = df_mul(A.get(i, r), di);  // U[i][r] = L[r][i]
+      for (int j = 2 * lane; j <= i; j += 64) {
+        float2 ah = A.hi2(i, j), al = A.lo2(i, j);
+        // R[i][i] = 1; column i + 1 of row r is not part of this step
+        if (j == i) ah.x = 1.f, al.x = 0.f;
+        if (j + 1 == i) ah.y = 1.f, al.y = 0.f;
+        float2 ch = A.hi2(r, j), cl = A.lo2(r, j);
+        const float2 oh = ch, ol = cl;
+        df2_fnma(ch, cl, w.hi, -w.hi, w.lo, ah, al);
+        if (j + 1 > i) ch.y = oh.y, cl.y = ol.y;
+        A.set2(r, j, ch, cl);
+      }
     }
     __syncthreads();
   }
-  // deferred scaling of the last row
-  const df dl = invd[n - 1];
-  for (int j = tid; j < n - 1; j += kThreads) A[j * ld + n - 1] = df_mul(A[j * ld + n - 1], dl);
+  for (int r = 1 + warp; r < n; r += kWarps) {
+    const df dr = invd[r];
+    for (int j = 2 * lane; j < r; j += 64) {
+      float2 ch = A.hi2(r, j), cl = A.lo2(r, j);
+      const float2 oh = ch, ol = cl;
+      df2_mul1(ch, cl, dr);
+      if (j + 1 >= r) ch.y = oh.y, cl.y = ol.y;  // the diagonal is not stored here
+      A.set2(r, j, ch, cl);
+    }
+  }
   __syncthreads();
 }
 
-// solve (L L^T) x = b in place (single right-hand side), L lower in A
-__device__ void chol_solve_df(const df* A, int n, int ld, const df* invd, df* x) {
+// solve (U^T U) x = b in place (single right-hand side), U upper in A
+__device__ void chol_solve_df(const DfMat& A, int n, const df* invd, df* x) {
   const int tid = threadIdx.x;
   for (int j = 0; j < n; ++j) {
     __syncthreads();
     if (tid == 0) x[j] = df_mul(x[j], invd[j]);
     __syncthreads();
-    for (int i = j + 1 + tid; i < n; i += kThreads) x[i] = df_sub(x[i], df_mul(A[i * ld + j], x[j]));
+    for (int i = j + 1 + tid; i < n; i += kThreads) x[i] = df_sub(x[i], df_mul(A.get(j, i), x[j]));
   }
   for (int j = n - 1; j >= 0; --j) {
     __syncthreads();
     if (tid == 0) x[j] = df_mul(x[j], invd[j]);
     __syncthreads();
-    for (int i = tid; i < j; i += kThreads) x[i] = df_sub(x[i], df_mul(A[j * ld + i], x[j]));
+    for (int i = tid; i < j; i += kThreads) x[i] = df_sub(x[i], df_mul(A.get(i, j), x[j]));
   }
   __syncthreads();
 }
@@ -267,7 +332,7 @@ __device__ void fail_partition(const Params& p, int part, bool init) {
 }  // namespace
 
 size_t solve_init_smem_bytes(int B, int BA) {
-  return ((size_t)BA * BA + 10 * (size_t)B) * sizeof(df) + 64;
+  return ((size_t)BA * BA + 12 * (size_t)B) * sizeof(df) + 64;
 }
 size_t solve_iter_smem_bytes(int B) {
   return ((size_t)B * B + 12 * (size_t)B + 8) * sizeof(df) + 64;
@@ -279,45 +344,43 @@ size_t solve_literal_smem_bytes(int B, int BA) {
 __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df red[kWarps];
-  __shared__ int s_flag;
   const int part = blockIdx.x;
   const int tid = threadIdx.x;
   const int B = p.B, BA = p.BA;
   const size_t pb = (size_t)part * B;
-  df* A = reinterpret_cast<df*>(smem_raw);
-  df* vm = A + (size_t)BA * BA;  // pilot m
+  const DfMat A{reinterpret_cast<float*>(smem_raw), BA, BA * BA};
+  df* vm = reinterpret_cast<df*>(smem_raw) + (size_t)BA * BA;  // pilot m
   df* vmu = vm + B;              // mu^0
   df* vu3 = vmu + B;             // m - mu^0, later mu^0 - mu0f
-  df* vz0 = vu3 + B;             // zeros (no b-coefficient at initialisation)
-  df* vt = vz0 + B;              // t^0
+  df* vt = vu3 + B;              // t^0
   df* vy = vt + B;
   df* vz = vy + B;
   df* invd = vz + B;
   df* vmf = invd + B;            // mu0f
+  df* scr = vmf + B;             // 3 B: assemble's coefficient vectors
   if (p.status[part] != MF_OK) return;  // the statistics pass timed out
 
   reduce_k1(p, part, A);
-  const df N = A[(B + 2) * BA + B + 2];
+  const df N = A.get(B + 2, B + 2);
   const bool enough = N.hi > (float)B;
   const df invN = enough ? df_recip(N) : df{0.f, 0.f};
-  const df sa = A[B * BA + B + 2];
+  const df sa = A.get(B, B + 2);
   for (int b = tid; b < B; b += kThreads) {
     const float m = p.pilot[pb + b];
     vm[b] = df{m, 0.f};
     // mu^0 = m + (sum e + (sum a) m) / N
-    const df mu = df_add(df{m, 0.f}, df_mul(df_fma(sa, df{m, 0.f}, A[b * BA + B + 2]), invN));
+    const df mu = df_add(df{m, 0.f}, df_mul(df_fma(sa, df{m, 0.f}, A.get(b, B + 2)), invN));
     vmu[b] = mu;
     vu3[b] = df_sub(df{m, 0.f}, mu);
-    vz0[b] = df{0.f, 0.f};
   }
   __syncthreads();
-  assemble(p, A, vm, vz0, vu3, invN, p.S + (size_t)part * B * B);
-  const bool ok = enough && cholesky_df(A, B, BA, invd, &s_flag);
+  assemble(p, A, vm, nullptr, vu3, invN, p.S + (size_t)part * B * B, scr);
+  const bool ok = enough && cholesky_upper_df(A, B, invd);
   if (!ok) {
     fail_partition(p, part, true);
     return;
   }
-  tri_inverse_df(A, B, BA, invd);
+  tri_inverse_df(A, B, invd);
   for (int b = tid; b < B; b += kThreads) {
     vt[b] = df_mulf(vmu[b], p.k[b]);
     const float mf = df_to_float(vmu[b]);
@@ -329,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
   for (int i = tid; i < B; i += kThreads) {
     Dot2 d;
     d.add(invd[i], vt[i]);
-    for (int j = 0; j < i; ++j) d.add(A[j * BA + i], vt[j]);
+    for (int j = 0; j < i; ++j) d.add(A.get(i, j), vt[j]);
     vy[i] = d.result();
   }
   __syncthreads();
@@ -337,7 +400,7 @@ __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
   for (int j = tid; j < B; j += kThreads) {
     Dot2 d;
     d.add(invd[j], vy[j]);
-    for (int i = j + 1; i < B; ++i) d.add(A[j * BA + i], vy[i]);
+    for (int i = j + 1; i < B; ++i) d.add(A.get(i, j), vy[i]);
     vz[j] = d.result();
   }
   __syncthreads();
@@ -349,7 +412,7 @@ __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
   float2* X = p.Linv + (size_t)part * B * B;
   for (int idx = tid; idx < B * B; idx += kThreads) {
     const int i = idx / B, j = idx % B;
-    const df v = (j < i) ? A[j * BA + i] : (j == i ? invd[i] : df{0.f, 0.f});
+    const df v = (j < i) ? A.get(i, j) : (j == i ? invd[i] : df{0.f, 0.f});
     stf(X, idx, v);
   }
   for (int b = tid; b < B; b += kThreads) {
@@ -539,23 +602,23 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
     // direct path: C^{k+1} = C^0 + U M U^T assembled in double-float (into
     // the L^{-1} buffer, no longer needed), factorised and solved
     const double* Sg = p.S + (size_t)part * B * B;
+    const DfMat Xm{reinterpret_cast<float*>(X), B, B * B};
     const df mvar = var, mb2 = df_mul(bbar, bbar);
     for (int idx = tid; idx < B * B; idx += kThreads) {
       const int i = idx / B, j = idx % B;
-      if (j > i) continue;
+      if (j < i) continue;  // upper triangle
       df c = df_from_double(Sg[idx]);
       c = df_sub(c, df_add(df_mul(U0[i], U1[j]), df_mul(U1[i], U0[j])));
       c = df_fma(mvar, df_mul(U1[i], U1[j]), c);
       c = df_fma(mb2, df_mul(U2[i], U2[j]), c);
-      X[idx] = c;
+      Xm.set(i, j, c);
     }
     for (int b = tid; b < B; b += kThreads) vv[b] = U1[b];
-    __shared__ int s_flag;
-    if (!cholesky_df(X, B, B, Y0, &s_flag)) {  // Y0 holds 1/diag(L)
+    if (!cholesky_upper_df(Xm, B, Y0)) {  // Y0 holds 1/diag(U)
       fail_partition(p, part, false);
       return;
     }
-    chol_solve_df(X, B, B, Y0, vv);
+    chol_solve_df(Xm, B, Y0, vv);
   } else {
     const df y0 = s_y[0], y1 = s_y[1], y2 = s_y[2];
     for (int b = tid; b < B; b += kThreads) {
@@ -594,14 +657,13 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
 __global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df red[kWarps];
-  __shared__ int s_flag;
   const int part = blockIdx.x;
   const int tid = threadIdx.x;
   const int B = p.B, BA = p.BA;
   const size_t pb = (size_t)part * B;
   if (p.status[part] != MF_OK) return;
-  df* A = reinterpret_cast<df*>(smem_raw);
-  df* u1 = A + (size_t)BA * BA;  // mu0f
+  const DfMat A{reinterpret_cast<float*>(smem_raw), BA, BA * BA};
+  df* u1 = reinterpret_cast<df*>(smem_raw) + (size_t)BA * BA;  // mu0f
   df* u2 = u1 + B;               // t^k
   df* u3 = u2 + B;               // mu0f - mu^k
   df* vz = u3 + B;
@@ -609,7 +671,7 @@ __global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p) {
   df* vd = invd + B;             // mu^k - mu0f
 
   reduce_k1(p, part, A);
-  const df N = A[(B + 2) * BA + B + 2];
+  const df N = A.get(B + 2, B + 2);
   const df invN = df_recip(N);
   for (int b = tid; b < B; b += kThreads) {
     const df mf{p.mu0f[pb + b], 0.f};
@@ -621,12 +683,12 @@ __global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p) {
     vz[b] = u2[b];
   }
   __syncthreads();
-  assemble(p, A, u1, u2, u3, invN, nullptr);
-  if (!cholesky_df(A, B, BA, invd, &s_flag)) {
+  assemble(p, A, u1, u2, u3, invN, nullptr, vd + B);
+  if (!cholesky_upper_df(A, B, invd)) {
     fail_partition(p, part, false);
     return;
   }
-  chol_solve_df(A, B, BA, invd, vz);
+  chol_solve_df(A, B, invd, vz);
   const df q = block_dot_df(u2, vz, B, red);
   const df muv = block_dot_df(u1, vz, B, red);
   const df coff = block_dot_df(vd, vz, B, red);
@@ -650,11 +712,11 @@ __global__ void __launch_bounds__(kThreads) background_kernel(Params p, double* 
   const int tid = threadIdx.x;
   const int B = p.B, BA = p.BA;
   const size_t pb = (size_t)part * B;
-  df* A = reinterpret_cast<df*>(smem_raw);
-  df* vm = A + (size_t)BA * BA;
+  const DfMat A{reinterpret_cast<float*>(smem_raw), BA, BA * BA};
+  df* vm = reinterpret_cast<df*>(smem_raw) + (size_t)BA * BA;
   df* vmu = vm + B;
   df* vu3 = vmu + B;
-  df* vz0 = vu3 + B;
+  df* scr = vu3 + B;  // 3 B: assemble's coefficient vectors
   double* cov = cov_out + (size_t)part * B * B;
   if (p.status[part] != MF_OK) {
     for (int idx = tid; idx < B * B; idx += kThreads) cov[idx] = __longlong_as_double(0x7ff8000000000000LL);
@@ -662,20 +724,19 @@ __global__ void __launch_bounds__(kThreads) background_kernel(Params p, double* 
     return;
   }
   reduce_k1(p, part, A);
-  const df N = A[(B + 2) * BA + B + 2];
+  const df N = A.get(B + 2, B + 2);
   const bool enough = N.hi > (float)B;
   const df invN = enough ? df_recip(N) : df{0.f, 0.f};
-  const df sa = A[B * BA + B + 2];
+  const df sa = A.get(B, B + 2);
   for (int b = tid; b < B; b += kThreads) {
     const float m = p.pilot[pb + b];
     vm[b] = df{m, 0.f};
-    const df mu = df_add(df{m, 0.f}, df_mul(df_fma(sa, df{m, 0.f}, A[b * BA + B + 2]), invN));
+    const df mu = df_add(df{m, 0.f}, df_mul(df_fma(sa, df{m, 0.f}, A.get(b, B + 2)), invN));
     vmu[b] = mu;
     vu3[b] = df_sub(df{m, 0.f}, mu);
-    vz0[b] = df{0.f, 0.f};
   }
   __syncthreads();
-  assemble(p, A, vm, vz0, vu3, invN, cov);
+  assemble(p, A, vm, nullptr, vu3, invN, cov, scr);
   for (int b = tid; b < B; b += kThreads)
     mu_out[pb + b] = enough ? df_to_double(vmu[b]) : __longlong_as_double(0x7ff8000000000000LL);
   if (!enough)
@@ -683,7 +744,7 @@ __global__ void __launch_bounds__(kThreads) background_kernel(Params p, double* 
 }
 
 size_t background_smem_bytes(int B, int BA) {
-  return ((size_t)BA * BA + 4 * (size_t)B) * sizeof(df) + 64;
+  return ((size_t)BA * BA + 6 * (size_t)B) * sizeof(df) + 64;
 }
 cudaError_t background_set_attributes(size_t smem) {
   return cudaFuncSetAttribute(background_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
