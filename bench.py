@@ -5,7 +5,11 @@ Workload: a synthetic AVIRIS-NG-shaped flightline, 4000 rows x 598 detector
 columns x 72 bands (2122-2488 nm) float32, 5% of pixels masked, 20 plume
 blobs; lambda = 1e-3, eps = 1e-9, 10 iterations, one partition per column.
 Metric: Mpixel/s = rows * cols / (seconds per retrieval), masked pixels
-counted.  One JSON line on stdout (rank 0).
+counted.  The headline form computes the background moments on the tensor
+cores (bf16 hi + lo split, float32 accumulation); the same schedule with
+float32 moments and the literal schedule of the algorithm figure (plain
+FP32) are timed beside it, each with its alpha error against the FP64
+oracle on sampled whole partitions.  One JSON line on stdout (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -265,14 +269,22 @@ def main():
             plan.profile(False)
         return ms, prof
 
-    # --- headline form: fused schedule, float32 pixel path, double-float solves
-    plan = mfg.Plan(rows, cols, bands, flags=mfg.ALBEDO | mfg.SPARSE)
+    # --- headline form: fused schedule, moments on the tensor cores (bf16
+    # hi + lo split, float32 accumulation), float32 pixel path, double-float
+    # solves
+    plan = mfg.Plan(rows, cols, bands, flags=mfg.ALBEDO | mfg.SPARSE, precision=mfg.BF16SPLIT)
     clk = ClockSampler(local)
     clk.start()
     ms, prof = timed(plan, args.steps, args.warmup, profile=True)
     clocks = clk.stop()
     ms_max = max_over_ranks(ms, world)
     value = world * npix / (ms_max * 1e-3) / 1e6
+    alpha_bf16 = out.clone()
+
+    # --- the same fused schedule with float32 (SIMT) moments
+    plan_f32 = mfg.Plan(rows, cols, bands, flags=mfg.ALBEDO | mfg.SPARSE)
+    f32_steps = max(2, args.steps // 4)
+    ms_f32, prof_f32 = timed(plan_f32, f32_steps, args.warmup, profile=True)
     alpha_fused = out.clone()
 
     # kernel-level roofline: pixel kernel, algorithmic bytes per launch
@@ -294,9 +306,19 @@ def main():
 
     # --- plain FP32 form (literal schedule of the algorithm figure)
     plan_lit = mfg.Plan(rows, cols, bands, flags=mfg.ALBEDO | mfg.SPARSE | mfg.LITERAL)
-    lit_steps = max(2, args.steps // 4)
-    ms_lit, _ = timed(plan_lit, lit_steps, 1)
+    lit_steps = max(2, args.steps // 8)
+    ms_lit, _ = timed(plan_lit, lit_steps, args.warmup)
     alpha_lit = out.clone()
+
+    # tensor-core statistics kernel: executed MMA work per launch (two
+    # tcgen05.mma per 16 pixels: M 128 x N 2 NP and M 128 x N NP, K 16)
+    st_ms, st_n = prof["stats"]
+    np_w = ((bands + 3 + 3) // 4 * 4 + 15) // 16 * 16
+    mma_flops = 2.0 * 128 * (3 * np_w) * npix
+    syrk = {"kernel": "stats_tc_kernel", "launches": int(st_n),
+            "avg_launch_us": st_ms / st_n * 1e3,
+            "tensor_tflops": mma_flops / (st_ms / st_n * 1e-3) / 1e12,
+            "hbm_gbs": npix * (4 * bands + 1) / (st_ms / st_n * 1e-3) / 1e9}
 
     # --- end to end through the host-buffer entry point (pinned memory)
     cube_h = sc.cube.cpu().pin_memory()
@@ -327,7 +349,8 @@ def main():
             sub = sc.cube[:, cols_s, :].cpu().numpy()
             msk = sc.mask[:, cols_s].cpu().numpy()
             valid = oracle.valid_pixels(sub, msk)
-            for name, a in (("fused", alpha_fused), ("literal", alpha_lit)):
+            for name, a in (("bf16split", alpha_bf16), ("fused", alpha_fused),
+                            ("literal", alpha_lit)):
                 g = a[:, cols_s].cpu().numpy().astype(np.float64)
                 d = np.abs(g - ref)[valid]
                 r = np.abs(ref[valid])
@@ -339,12 +362,15 @@ def main():
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (moments: bf16 hi+lo products, f32 accumulation)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "rows": rows, "cols": cols, "bands": bands,
                        "n_iter": n_iter, "lambda": prm["lam"], "eps": prm["eps"],
                        "mask_frac": 0.05, "partitions": cols,
-                       "form": "fused schedule, float32 pixel path, double-float solves",
+                       "form": "fused schedule; moments on tcgen05 tensor cores from bf16 "
+                               "hi+lo split with f32 accumulation; float32 pixel path; "
+                               "double-float Cholesky and solves",
                        "l2": "inputs larger than L2 (689 MB cube per step)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"kernel": "pixel_kernel", "bound": "hbm", "achieved": achieved,
@@ -357,12 +383,18 @@ def main():
             "kernels_ms_per_step": {"stats": st_ms / args.steps, "pixel": px_ms / args.steps,
                                     "solve": sv_ms / args.steps},
             "gpu_launches": launches,
-            "forms": {"fused": {"value": value, "ms_per_step": ms_max,
-                                "alpha_error": err.get("fused")},
+            "syrk": syrk,
+            "forms": {"bf16split_fused": {"value": value, "ms_per_step": ms_max,
+                                          "alpha_error": err.get("bf16split")},
+                      "fp32_fused": {"value": world * npix / (ms_f32 * 1e-3) / 1e6,
+                                     "ms_per_step": ms_f32,
+                                     "kernels_ms_per_step": {
+                                         k: v[0] / f32_steps for k, v in prof_f32.items()},
+                                     "alpha_error": err.get("fused")},
                       "plain_fp32_literal": {"value": world * npix / (ms_lit * 1e-3) / 1e6,
                                              "ms_per_step": ms_lit,
                                              "alpha_error": err.get("literal")}},
-            "alpha_error": err.get("fused"),
+            "alpha_error": err.get("bf16split"),
             "e2e": {"value": world * npix / e2e_s / 1e6, "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "api": "mf_retrieve_host (pinned host buffers)"},
@@ -371,6 +403,7 @@ def main():
         }
         print(json.dumps(result), flush=True)
     plan.close()
+    plan_f32.close()
     plan_lit.close()
     if world > 1:
         import torch.distributed as dist
