@@ -121,6 +121,32 @@ mf_status mf_retrieve_host(mf_plan_t plan, const float* cube, const float* k, do
                            double eps, int32_t n_iter, const uint8_t* mask,
                            float* alpha_out, void* stream);
 
+/* Batched form: many flightlines of uneven length in one retrieval.  The
+ * lines are stacked along rows in one BIP cube: line l is rows
+ * [line_rows[0] + ... + line_rows[l-1], ... + line_rows[l]) and desc->rows is
+ * the sum; cols, the band window, col_group, precision and flags are shared.
+ * Every line has its own partitions (Sec. II-E), P = n_lines x
+ * ceil(cols / col_group) in all, line-major, and its own statistics, lambda
+ * and iteration count; every kernel of the retrieval covers all lines at once
+ * (a line whose iterations are done skips the later passes).  Errors as
+ * mf_plan; line_rows (host, n_lines) must be positive. */
+mf_status mf_plan_batched(const mf_desc* desc, const int64_t* line_rows, int32_t n_lines,
+                          mf_plan_t* out);
+
+/* Number of lines of a plan (1 for mf_plan), or -1 for a null plan. */
+int32_t mf_num_lines(mf_plan_t plan);
+
+/* One retrieval of every line of a batched plan, enqueued on `stream`
+ * (Fig. 1 per line).  cube, mask, alpha_out: device, stacked as the plan's
+ * lines (rows = sum of line rows); k: device, B float32, shared; lambda and
+ * n_iter: HOST arrays of n_lines (copied before return; lambda >= 0 finite,
+ * 0 <= n_iter <= 100000); eps > 0 shared.  No alpha_init or albedo output.
+ * Allocates nothing; does not synchronise unless lambda or n_iter changed
+ * since the previous call (it then waits for that call's table upload). */
+mf_status mf_retrieve_batched(mf_plan_t plan, const float* cube, const float* k,
+                              const double* lambda, double eps, const int32_t* n_iter,
+                              const uint8_t* mask, float* alpha_out, void* stream);
+
 /* Background statistics of the last retrieval's initialisation (Fig. 1,
  * initial mean and covariance): mu0 (P, B) and cov0 (P, B, B), float64
  * DEVICE buffers.  Ordered after the retrieval on `stream`; synchronises it

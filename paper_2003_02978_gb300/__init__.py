@@ -33,7 +33,7 @@ TABLE_I = {
     "albedo_rwl1mf": (True, ALBEDO | SPARSE),
 }
 
-__all__ = ["Plan", "retrieve", "MFError", "ALBEDO", "SPARSE", "LITERAL", "PENALTY_NO_ALBEDO",
+__all__ = ["Plan", "BatchPlan", "retrieve", "MFError", "ALBEDO", "SPARSE", "LITERAL", "PENALTY_NO_ALBEDO",
            "FP32", "BF16SPLIT", "TABLE_I", "library_path"]
 
 
@@ -160,6 +160,65 @@ class Plan:
         n = (ctypes.c_int64 * 3)()
         check(lib().mf_profile_read(self._h, ms, n, 3), "mf_profile_read")
         return {"stats": (ms[0], n[0]), "pixel": (ms[1], n[1]), "solve": (ms[2], n[2])}
+
+
+class BatchPlan(Plan):
+    """A plan over many flightlines stacked along rows (``line_rows[l]`` rows
+    each; same cols, band window, flags and precision): one retrieval covers
+    every line, each with its own partitions, lambda and iteration count."""
+
+    def __init__(self, line_rows, cols, bands_total, band_lo=0, band_hi=None, col_group=1,
+                 flags=DEFAULT_FLAGS, precision=FP32):
+        line_rows = [int(r) for r in line_rows]
+        band_hi = bands_total if band_hi is None else band_hi
+        rows = sum(line_rows)
+        self.shape = Shape(rows, int(cols), int(bands_total), int(band_lo), int(band_hi),
+                           int(col_group), int(flags), int(precision))
+        d = MfDesc(rows=rows, cols=cols, bands_total=bands_total, band_lo=band_lo,
+                   band_hi=band_hi, col_group=col_group, layout=0, precision=precision,
+                   flags=flags)
+        lr = (ctypes.c_int64 * len(line_rows))(*line_rows)
+        h = ctypes.c_void_p()
+        check(lib().mf_plan_batched(ctypes.byref(d), lr, len(line_rows), ctypes.byref(h)),
+              "mf_plan_batched")
+        self._h = h
+        self.line_rows = line_rows
+        self.n_lines = int(lib().mf_num_lines(h))
+        self.B = band_hi - band_lo
+        self.P = int(lib().mf_num_partitions(h))
+
+    def retrieve(self, cube, k, lam, eps, n_iter, mask=None, out=None, stream=None):
+        """Enqueue one retrieval of every line.  ``lam`` and ``n_iter`` are
+        per-line sequences (or scalars for all lines); returns ``out``
+        (total rows, cols) float32 alpha, stacked like the cube."""
+        s = self.shape
+        self._check_cube(cube)
+        k = torch.as_tensor(k, dtype=torch.float32, device=cube.device).contiguous()
+        if k.numel() != self.B:
+            raise ValueError(f"k must have {self.B} entries")
+        lam = np.broadcast_to(np.asarray(lam, dtype=np.float64), (self.n_lines,))
+        n_iter = np.broadcast_to(np.asarray(n_iter, dtype=np.int32), (self.n_lines,))
+        lam_c = (ctypes.c_double * self.n_lines)(*lam.tolist())
+        nit_c = (ctypes.c_int32 * self.n_lines)(*n_iter.tolist())
+        if mask is not None:
+            if mask.dtype != torch.uint8 or tuple(mask.shape) != (s.rows, s.cols) or \
+                    not mask.is_cuda or not mask.is_contiguous():
+                raise ValueError("mask must be a contiguous CUDA uint8 (rows, cols) tensor")
+        if out is None:
+            out = torch.empty((s.rows, s.cols), dtype=torch.float32, device=cube.device)
+        check(lib().mf_retrieve_batched(self._h, _ptr(cube), _ptr(k), lam_c, float(eps), nit_c,
+                                        _ptr(mask), _ptr(out), _stream_handle(stream)),
+              "mf_retrieve_batched")
+        self._k_keepalive = k
+        return out
+
+    def line_slices(self):
+        """Row slice of every line in the stacked cube."""
+        out, r0 = [], 0
+        for r in self.line_rows:
+            out.append(slice(r0, r0 + r))
+            r0 += r
+        return out
 
 
 _PLANS: dict = {}

@@ -56,6 +56,13 @@ def lib() -> ctypes.CDLL:
     L.mf_last_error.restype = c_char_p
     L.mf_background_noalloc.argtypes = [POINTER(MfDesc), fp, fp, fp, fp, c_void_p]
     L.mf_background_noalloc.restype = c_int
+    L.mf_plan_batched.argtypes = [POINTER(MfDesc), POINTER(c_int64), c_int32, POINTER(c_void_p)]
+    L.mf_plan_batched.restype = c_int
+    L.mf_num_lines.argtypes = [c_void_p]
+    L.mf_num_lines.restype = c_int32
+    L.mf_retrieve_batched.argtypes = [c_void_p, fp, fp, POINTER(c_double), c_double,
+                                      POINTER(c_int32), fp, fp, c_void_p]
+    L.mf_retrieve_batched.restype = c_int
     for name, args in (("mf_profile", [c_void_p, c_int32]),
                        ("mf_profile_read", [c_void_p, POINTER(c_double), POINTER(c_int64),
                                             c_int32])):

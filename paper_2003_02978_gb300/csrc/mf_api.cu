@@ -58,6 +58,13 @@ struct mf_plan_s {
   int nj = 0;             // template bucket
   size_t smem_stats = 0, smem_pixel = 0, smem_sinit = 0, smem_siter = 0, smem_slit = 0;
   int grid_stats = 0, grid_pixel = 0;
+  // flightlines: host copy of the device table, pinned staging for the
+  // per-call lambda / iteration counts, and the values last uploaded
+  int n_lines = 1;
+  std::vector<mf::LineInfo> lines;
+  mf::LineInfo* lines_pinned = nullptr;
+  cudaEvent_t lines_copied = nullptr;
+  bool lines_valid = false;
   // tensor maps of the last cube pointer (re-encoded when it changes)
   const float* map_cube = nullptr;
   CUtensorMap map_stats{}, map_pixel{};
@@ -164,20 +171,22 @@ void mark_end(mf_plan_s::Mark* m, cudaStream_t s) {
 
 enum { KIND_STATS = 0, KIND_PIXEL = 1, KIND_SOLVE = 2, KIND_COUNT = 3 };
 
-void stats_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, cudaStream_t s) {
+void stats_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int pass, cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_STATS, s);
   if (pl->d.precision == MF_BF16SPLIT) {
     // persistent: one CTA per SM over the (column, chunk) work items
     if (mode == mf::STAT_INIT) mf::pilot_launch(s, prm);
     const int grid = std::min(pl->grid_stats, pl->num_sms);
-    mf::stats_tc_launch(pl->nj, grid, pl->smem_stats, s, pl->map_stats, prm, mode);
+    mf::stats_tc_launch(pl->nj, grid, pl->smem_stats, s, pl->map_stats, prm, mode, pass);
   } else
-    mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, pl->map_stats, prm, mode);
+    mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, pl->map_stats, prm, mode, pass);
   mark_end(m, s);
 }
-void pixel_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int acc, cudaStream_t s) {
+void pixel_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int acc, int pass,
+                    cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_PIXEL, s);
-  mf::pixel_launch(pl->nj, pl->grid_pixel, pl->smem_pixel, s, pl->map_pixel, prm, mode, acc);
+  mf::pixel_launch(pl->nj, pl->grid_pixel, pl->smem_pixel, s, pl->map_pixel, prm, mode, acc,
+                   pass);
   mark_end(m, s);
 }
 void solve_init_dispatch(mf_plan_s* pl, const mf::Params& prm, cudaStream_t s) {
@@ -185,14 +194,15 @@ void solve_init_dispatch(mf_plan_s* pl, const mf::Params& prm, cudaStream_t s) {
   mf::solve_init_launch(pl->smem_sinit, s, prm);
   mark_end(m, s);
 }
-void solve_iter_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, cudaStream_t s) {
+void solve_iter_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int pass,
+                         cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_SOLVE, s);
-  mf::solve_iter_launch(pl->smem_siter, s, prm, mode);
+  mf::solve_iter_launch(pl->smem_siter, s, prm, mode, pass);
   mark_end(m, s);
 }
-void solve_literal_dispatch(mf_plan_s* pl, const mf::Params& prm, cudaStream_t s) {
+void solve_literal_dispatch(mf_plan_s* pl, const mf::Params& prm, int pass, cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_SOLVE, s);
-  mf::solve_literal_launch(pl->smem_slit, s, prm);
+  mf::solve_literal_launch(pl->smem_slit, s, prm, pass);
   mark_end(m, s);
 }
 
@@ -217,12 +227,27 @@ const char* mf_status_string(mf_status s) {
 
 const char* mf_last_error(void) { return g_last_error.c_str(); }
 
-mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
-  g_last_error.clear();
+}  // extern "C"
+
+namespace {
+
+// Validate the descriptor and build a plan over n_lines flightlines stacked
+// along rows (line_rows[l] rows each; d->rows is their sum).
+mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines, mf_plan_t* out) {
   if (!d || !out) return fail(MF_ERR_INVALID_ARG, "null descriptor or output");
   *out = nullptr;
   if (d->rows <= 0 || d->cols <= 0 || d->bands_total <= 0)
     return fail(MF_ERR_INVALID_ARG, "rows, cols and bands_total must be positive");
+  if (n_lines < 1 || n_lines > (1 << 20)) return fail(MF_ERR_INVALID_ARG, "n_lines = %d", n_lines);
+  int64_t sum = 0;
+  for (int l = 0; l < n_lines; ++l) {
+    if (line_rows[l] <= 0) return fail(MF_ERR_INVALID_ARG, "line %d has %lld rows", l,
+                                       (long long)line_rows[l]);
+    sum += line_rows[l];
+  }
+  if (sum != d->rows)
+    return fail(MF_ERR_INVALID_ARG, "rows %lld != sum of the line rows %lld", (long long)d->rows,
+                (long long)sum);
   if (d->band_lo < 0 || d->band_hi > d->bands_total || d->band_hi <= d->band_lo)
     return fail(MF_ERR_INVALID_ARG, "band window [%d, %d) outside [0, %lld)", d->band_lo,
                 d->band_hi, (long long)d->bands_total);
@@ -245,6 +270,7 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
 
   mf_plan_s* pl = new mf_plan_s();
   pl->d = *d;
+  pl->n_lines = n_lines;
   mf::Params& p = pl->prm;
   p.rows = (int)d->rows;
   p.cols = (int)d->cols;
@@ -253,9 +279,11 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
   p.B = B;
   p.B4 = B / 4;
   p.G = (int)std::min<int64_t>(d->col_group, d->cols);
-  p.P = (p.cols + p.G - 1) / p.G;
+  p.Pl = (p.cols + p.G - 1) / p.G;
+  p.P = n_lines * p.Pl;
   p.BA = (B + 3 + 3) / 4 * 4;
   p.flags = d->flags;
+  p.n_lines = n_lines;
   pl->nj = nj_bucket(p.B4);
 
   cudaError_t e = cudaGetDevice(&pl->device);
@@ -265,35 +293,63 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
     delete pl;
     return fail(MF_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
   }
-  // row blocking: pixel kernel blocks of rb rows (a multiple of the stage
-  // height), as few as fill the SMs once (column tiles x row blocks ~ the
-  // resident pixel CTAs per SM x SM count); statistics chunks sized so that the
-  // statistics grid has several CTAs per SM
+  // Row blocking.  Pixel kernel: blocks of about h_p rows (a multiple of the
+  // stage height), as few as fill the SMs once (column tiles x row blocks ~
+  // the resident pixel CTAs per SM x SM count), at most 512 rows so that a
+  // batch of long lines has no long CTAs at its end.  Statistics: chunks of
+  // about h_s rows so that the SIMT grid has several CTAs per SM, at most
+  // 1024 rows in the tensor-core form (float32 sums in tensor memory) and
+  // 2048 otherwise.  Every line is split evenly into whole blocks / chunks.
   p.n_ct = (p.cols + mf::kTileCols - 1) / mf::kTileCols;
-  int rb = env_int("MF_RB_ROWS", 0);
-  if (rb <= 0) {
+  int hp = env_int("MF_RB_ROWS", 0);
+  if (hp <= 0) {
     const long waves = (long)mf::pixel_ctas_per_sm(pl->nj) * pl->num_sms;
     const long nrb = std::max<long>(1, (waves + p.n_ct - 1) / p.n_ct);
-    rb = (int)((p.rows + nrb - 1) / nrb);
+    hp = (int)std::min<long>(512, (p.rows + nrb - 1) / nrb);
   }
-  rb = std::max(rb, mf::kStageRows);
-  rb = (rb + mf::kStageRows - 1) / mf::kStageRows * mf::kStageRows;
-  p.rb_rows = std::min(rb, (p.rows + mf::kStageRows - 1) / mf::kStageRows * mf::kStageRows);
-  p.n_rb = (p.rows + p.rb_rows - 1) / p.rb_rows;
-  int sc = env_int("MF_SC_ROWS", 0);
-  if (sc <= 0) {
+  hp = std::max(hp, mf::kStageRows);
+  int hs = env_int("MF_SC_ROWS", 0);
+  if (hs <= 0) {
     const long target_ctas = 2400;
-    long nsc = std::max<long>(1, (target_ctas + p.cols - 1) / p.cols);
-    sc = (int)((p.rows + nsc - 1) / nsc);
-    // the tensor-core form accumulates a chunk in float32 in tensor memory:
-    // at most 1024 rows per chunk keeps that sum within the stated bound
-    if (d->precision == MF_BF16SPLIT) sc = std::min(sc, 1024);
+    const long nsc = std::max<long>(1, (target_ctas + p.cols - 1) / p.cols);
+    hs = (int)std::min<long>(d->precision == MF_BF16SPLIT ? 1024 : 2048, (p.rows + nsc - 1) / nsc);
   }
-  sc = std::max(mf::kStatRows, (sc + mf::kStatRows - 1) / mf::kStatRows * mf::kStatRows);
-  p.sc_rows = sc;
-  p.n_sc = (p.rows + p.sc_rows - 1) / p.sc_rows;
-  pl->grid_stats = p.cols * p.n_sc;
-  pl->grid_pixel = p.n_ct * p.n_rb;
+  hs = std::max(hs, mf::kStatRows);
+  auto round_up = [](int x, int m) { return (x + m - 1) / m * m; };
+  pl->lines.resize(n_lines);
+  int row0 = 0;
+  long long items = 0, blocks = 0, k1u = 0, k3u = 0;
+  for (int l = 0; l < n_lines; ++l) {
+    mf::LineInfo& L = pl->lines[l];
+    L = mf::LineInfo{};
+    L.row0 = row0;
+    L.rows = (int)line_rows[l];
+    L.n_sc = (L.rows + hs - 1) / hs;
+    L.sc_rows = round_up((L.rows + L.n_sc - 1) / L.n_sc, mf::kStatRows);
+    L.n_sc = (L.rows + L.sc_rows - 1) / L.sc_rows;
+    L.n_rb = (L.rows + hp - 1) / hp;
+    L.rb_rows = round_up((L.rows + L.n_rb - 1) / L.n_rb, mf::kStageRows);
+    L.n_rb = (L.rows + L.rb_rows - 1) / L.rb_rows;
+    L.item0 = (int)items;
+    L.blk0 = (int)blocks;
+    L.k1u0 = k1u;
+    L.k3u0 = k3u;
+    L.n_iter = 0;
+    L.lambda = 0.f;
+    items += (long long)p.cols * L.n_sc;
+    blocks += (long long)p.n_ct * L.n_rb;
+    k1u += (long long)p.cols * L.n_sc;
+    k3u += (long long)p.cols * L.n_rb;
+    row0 += L.rows;
+  }
+  if (items > INT32_MAX || blocks > INT32_MAX) {
+    delete pl;
+    return fail(MF_ERR_UNSUPPORTED, "batch too large for one launch grid");
+  }
+  p.n_items = (int)items;
+  p.n_blocks = (int)blocks;
+  pl->grid_stats = p.n_items;
+  pl->grid_pixel = p.n_blocks;
   pl->smem_stats = d->precision == MF_BF16SPLIT ? mf::stats_tc_smem_bytes(B)
                                                  : mf::stats_smem_bytes(B);
   pl->smem_pixel = mf::pixel_smem_bytes(B, pl->nj);
@@ -304,11 +360,13 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
   // workspace
   const size_t P = (size_t)p.P;
   const size_t K1E = mf::k1_entries(p.BA), K3E = mf::k3_entries(B);
+  mf::LineInfo* lines_d = nullptr;
   struct Piece {
     void** dst;
     size_t bytes;
   };
   Piece pieces[] = {
+      {(void**)&lines_d, (size_t)n_lines * sizeof(mf::LineInfo)},
       {(void**)&p.pilot, P * B * sizeof(float)},
       {(void**)&p.mu0, P * B * sizeof(float2)},
       {(void**)&p.mu0f, P * B * sizeof(float)},
@@ -320,8 +378,8 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
       {(void**)&p.Linv, P * B * B * sizeof(float2)},
       {(void**)&p.pscal, P * 4 * sizeof(float)},
       {(void**)&p.dscal, P * 4 * sizeof(double)},
-      {(void**)&p.k1part, P * p.G * p.n_sc * K1E * sizeof(float2)},
-      {(void**)&p.k3part, P * p.G * p.n_rb * K3E * sizeof(float)},
+      {(void**)&p.k1part, (size_t)k1u * K1E * sizeof(float2)},
+      {(void**)&p.k3part, (size_t)k3u * K3E * sizeof(float)},
       {(void**)&p.status, P * sizeof(int)},
   };
   size_t total = 0;
@@ -340,16 +398,115 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
     *pc.dst = static_cast<char*>(pl->ws) + off;
     off += align_up(pc.bytes, 256);
   }
+  p.lines = lines_d;
   e = cudaMemset(pl->ws, 0, total);
+  if (e == cudaSuccess)
+    e = cudaMallocHost(&pl->lines_pinned, (size_t)n_lines * sizeof(mf::LineInfo));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->lines_copied, cudaEventDisableTiming);
   if (e == cudaSuccess) e = set_attrs(pl);
   if (e != cudaSuccess) {
     cudaFree(pl->ws);
+    if (pl->lines_pinned) cudaFreeHost(pl->lines_pinned);
+    if (pl->lines_copied) cudaEventDestroy(pl->lines_copied);
     delete pl;
     return fail(MF_ERR_CUDA, "plan set-up: %s", cudaGetErrorString(e));
   }
   *out = pl;
   return MF_OK;
 }
+
+// Upload the per-line lambda and iteration counts when they differ from the
+// values on the device (the staging buffer is reused once its last copy ran).
+mf_status upload_lines(mf_plan_s* pl, const double* lambda, const int32_t* n_iter,
+                       cudaStream_t s) {
+  bool same = pl->lines_valid;
+  for (int l = 0; l < pl->n_lines && same; ++l)
+    same = pl->lines[l].lambda == (float)lambda[l] && pl->lines[l].n_iter == n_iter[l];
+  if (same) return MF_OK;
+  for (int l = 0; l < pl->n_lines; ++l) {
+    pl->lines[l].lambda = (float)lambda[l];
+    pl->lines[l].n_iter = n_iter[l];
+  }
+  MF_CUDA(cudaEventSynchronize(pl->lines_copied));
+  std::memcpy(pl->lines_pinned, pl->lines.data(), (size_t)pl->n_lines * sizeof(mf::LineInfo));
+  MF_CUDA(cudaMemcpyAsync(const_cast<mf::LineInfo*>(pl->prm.lines), pl->lines_pinned,
+                          (size_t)pl->n_lines * sizeof(mf::LineInfo), cudaMemcpyHostToDevice, s));
+  MF_CUDA(cudaEventRecord(pl->lines_copied, s));
+  pl->lines_valid = true;
+  return MF_OK;
+}
+
+// Enqueue one retrieval of every line (lines with fewer iterations skip the
+// later passes inside the kernels).
+mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double eps,
+                        int32_t n_iter_max, const uint8_t* mask, const float* alpha_init,
+                        float* alpha_out, float* albedo_out, cudaStream_t s) {
+  if ((reinterpret_cast<uintptr_t>(cube) & 15) != 0)
+    return fail(MF_ERR_INVALID_ARG, "cube must be 16-byte aligned");
+  mf::Params p = pl->prm;
+  p.cube = cube;
+  p.k = k;
+  p.mask = mask;
+  p.alpha_init = alpha_init;
+  p.alpha = alpha_out;
+  p.albedo = albedo_out;
+  p.eps = (float)eps;
+  const bool literal = (p.flags & MF_LITERAL) != 0;
+  if (cube != pl->map_cube) {
+    if (!encode_cube_map(&pl->map_stats, pl->prm, cube, 1, mf::kStatRows) ||
+        !encode_cube_map(&pl->map_pixel, pl->prm, cube, mf::kTileCols, mf::kStageRows)) {
+      pl->map_cube = nullptr;
+      return fail(MF_ERR_CUDA, "cuTensorMapEncodeTiled failed for the cube");
+    }
+    pl->map_cube = cube;
+  }
+  MF_CUDA(cudaMemsetAsync(p.status, 0, (size_t)p.P * sizeof(int), s));
+  stats_dispatch(pl, p, mf::STAT_INIT, 0, s);
+  solve_init_dispatch(pl, p, s);
+  pixel_dispatch(pl, p, mf::PIX_INIT, n_iter_max > 0, 0, s);
+  for (int it = 1; it <= n_iter_max; ++it) {
+    if (literal) {
+      solve_iter_dispatch(pl, p, mf::SOLVE_MEAN_ONLY, it, s);
+      stats_dispatch(pl, p, mf::STAT_LITERAL, it, s);
+      solve_literal_dispatch(pl, p, it, s);
+    } else {
+      solve_iter_dispatch(pl, p, mf::SOLVE_FUSED, it, s);
+    }
+    pixel_dispatch(pl, p, mf::PIX_ITER, it < n_iter_max, it, s);
+  }
+  MF_CUDA(cudaGetLastError());
+  pl->last_stream = s;
+  return MF_OK;
+}
+
+mf_status check_scalars(double lambda, double eps, int32_t n_iter) {
+  if (n_iter < 0 || n_iter > 100000) return fail(MF_ERR_INVALID_ARG, "n_iter = %d", n_iter);
+  if (!std::isfinite(lambda) || !std::isfinite(eps))
+    return fail(MF_ERR_NONFINITE_INPUT, "lambda or eps not finite");
+  if (lambda < 0.0 || !(eps > 0.0))
+    return fail(MF_ERR_INVALID_ARG, "need lambda >= 0 and eps > 0");
+  return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
+  g_last_error.clear();
+  if (!d || !out) return fail(MF_ERR_INVALID_ARG, "null descriptor or output");
+  const int64_t rows = d->rows;
+  return build_plan(d, &rows, 1, out);
+}
+
+mf_status mf_plan_batched(const mf_desc* d, const int64_t* line_rows, int32_t n_lines,
+                          mf_plan_t* out) {
+  g_last_error.clear();
+  if (!line_rows) return fail(MF_ERR_INVALID_ARG, "null line_rows");
+  return build_plan(d, line_rows, n_lines, out);
+}
+
+int32_t mf_num_lines(mf_plan_t pl) { return pl ? pl->n_lines : -1; }
 
 void mf_destroy(mf_plan_t pl) {
   if (!pl) return;
@@ -363,6 +520,8 @@ void mf_destroy(mf_plan_t pl) {
   cudaFree(pl->h_mask);
   cudaFree(pl->h_k);
   cudaFree(pl->h_alpha);
+  if (pl->lines_pinned) cudaFreeHost(pl->lines_pinned);
+  if (pl->lines_copied) cudaEventDestroy(pl->lines_copied);
   delete pl;
 }
 
@@ -374,50 +533,33 @@ mf_status mf_retrieve(mf_plan_t pl, const float* cube, const float* k, double la
   g_last_error.clear();
   if (!pl) return fail(MF_ERR_INVALID_ARG, "null plan");
   if (!cube || !k || !alpha_out) return fail(MF_ERR_INVALID_ARG, "null cube, k or alpha_out");
-  if (n_iter < 0 || n_iter > 100000) return fail(MF_ERR_INVALID_ARG, "n_iter = %d", n_iter);
-  if (!std::isfinite(lambda) || !std::isfinite(eps))
-    return fail(MF_ERR_NONFINITE_INPUT, "lambda or eps not finite");
-  if (lambda < 0.0 || !(eps > 0.0))
-    return fail(MF_ERR_INVALID_ARG, "need lambda >= 0 and eps > 0");
-  if ((reinterpret_cast<uintptr_t>(cube) & 15) != 0)
-    return fail(MF_ERR_INVALID_ARG, "cube must be 16-byte aligned");
+  if (pl->n_lines != 1)
+    return fail(MF_ERR_INVALID_ARG, "plan of %d lines: use mf_retrieve_batched", pl->n_lines);
+  mf_status st = check_scalars(lambda, eps, n_iter);
+  if (st != MF_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  mf::Params p = pl->prm;
-  p.cube = cube;
-  p.k = k;
-  p.mask = mask;
-  p.alpha_init = alpha_init;
-  p.alpha = alpha_out;
-  p.albedo = albedo_out;
-  p.lambda = (float)lambda;
-  p.eps = (float)eps;
-  p.n_iter = n_iter;
-  const bool literal = (p.flags & MF_LITERAL) != 0;
-  if (cube != pl->map_cube) {
-    if (!encode_cube_map(&pl->map_stats, pl->prm, cube, 1, mf::kStatRows) ||
-        !encode_cube_map(&pl->map_pixel, pl->prm, cube, mf::kTileCols, mf::kStageRows)) {
-      pl->map_cube = nullptr;
-      return fail(MF_ERR_CUDA, "cuTensorMapEncodeTiled failed for the cube");
-    }
-    pl->map_cube = cube;
+  st = upload_lines(pl, &lambda, &n_iter, s);
+  if (st != MF_OK) return st;
+  return run_retrieval(pl, cube, k, eps, n_iter, mask, alpha_init, alpha_out, albedo_out, s);
+}
+
+mf_status mf_retrieve_batched(mf_plan_t pl, const float* cube, const float* k,
+                              const double* lambda, double eps, const int32_t* n_iter,
+                              const uint8_t* mask, float* alpha_out, void* stream) {
+  g_last_error.clear();
+  if (!pl) return fail(MF_ERR_INVALID_ARG, "null plan");
+  if (!cube || !k || !alpha_out || !lambda || !n_iter)
+    return fail(MF_ERR_INVALID_ARG, "null cube, k, lambda, n_iter or alpha_out");
+  int32_t n_max = 0;
+  for (int l = 0; l < pl->n_lines; ++l) {
+    mf_status st = check_scalars(lambda[l], eps, n_iter[l]);
+    if (st != MF_OK) return st;
+    n_max = std::max(n_max, n_iter[l]);
   }
-  MF_CUDA(cudaMemsetAsync(p.status, 0, (size_t)p.P * sizeof(int), s));
-  stats_dispatch(pl, p, mf::STAT_INIT, s);
-  solve_init_dispatch(pl, p, s);
-  pixel_dispatch(pl, p, mf::PIX_INIT, n_iter > 0, s);
-  for (int it = 1; it <= n_iter; ++it) {
-    if (literal) {
-      solve_iter_dispatch(pl, p, mf::SOLVE_MEAN_ONLY, s);
-      stats_dispatch(pl, p, mf::STAT_LITERAL, s);
-      solve_literal_dispatch(pl, p, s);
-    } else {
-      solve_iter_dispatch(pl, p, mf::SOLVE_FUSED, s);
-    }
-    pixel_dispatch(pl, p, mf::PIX_ITER, it < n_iter, s);
-  }
-  MF_CUDA(cudaGetLastError());
-  pl->last_stream = s;
-  return MF_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mf_status st = upload_lines(pl, lambda, n_iter, s);
+  if (st != MF_OK) return st;
+  return run_retrieval(pl, cube, k, eps, n_max, mask, nullptr, alpha_out, nullptr, s);
 }
 
 mf_status mf_retrieve_host(mf_plan_t pl, const float* cube, const float* k, double lambda,

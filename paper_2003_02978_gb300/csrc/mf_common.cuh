@@ -1,8 +1,11 @@
 // Shared definitions of the matched-filter kernels (sm_103a).
 //
 // Data layout in HBM (one plan; P partitions, B bands in the window):
-//   cube       caller's (rows, cols, bands_total) float32, BIP; window [band_lo, band_hi)
+//   cube       caller's (rows, cols, bands_total) float32, BIP; window [band_lo, band_hi);
+//              a batch of flightlines is stacked along rows (line l = rows
+//              [row0_l, row0_l + rows_l)), each line with its own partitions
 //   alpha      caller's (rows, cols) float32, updated in place every pass
+//   lines      (n_lines) LineInfo      per-line geometry, lambda and iteration count
 //   pilot      (P, B) float32        reference direction m of the initial statistics
 //   mu0        (P, B) double-float   initial mean mu^0
 //   mu0f       (P, B) float32        mu^0 rounded, as the pixel kernel holds it
@@ -38,16 +41,34 @@ enum : int { STAT_INIT = 0, STAT_LITERAL = 1 };
 enum : int { PIX_INIT = 0, PIX_ITER = 1 };
 enum : int { SOLVE_FUSED = 0, SOLVE_MEAN_ONLY = 1 };
 
+// One flightline of a plan (a single retrieval has one).  Its statistics
+// work items are (chunk, column), chunk-major, numbered from item0; its pixel
+// CTAs are (row block, column tile), row-block-major, numbered from blk0; the
+// per-CTA moment units of (column c, chunk) are k1u0 + c n_sc + chunk and of
+// (column c, row block) k3u0 + c n_rb + rb, so a partition's units are
+// contiguous.
+struct LineInfo {
+  int row0, rows;         // rows [row0, row0 + rows) of the stacked cube
+  int n_sc, sc_rows;      // statistics chunks (sc_rows a multiple of kStatRows)
+  int item0;              // first statistics item
+  int n_rb, rb_rows;      // pixel row blocks (rb_rows a multiple of kStageRows)
+  int blk0;               // first pixel CTA
+  int n_iter;             // reweighting iterations N_iter of the line
+  float lambda;           // multiplier on the weights of Eq. (5)
+  int pad_;
+  long long k1u0, k3u0;   // first moment units
+};
+
 struct Params {
   // geometry
-  int rows, cols, bands_total, band_lo, B, B4, G, P;
-  int rb_rows, n_rb;      // pixel kernel row blocks (multiple of kStageRows)
-  int sc_rows, n_sc;      // statistics kernel row chunks (multiple of kStatRows)
+  int rows, cols, bands_total, band_lo, B, B4, G;
+  int Pl, P;              // partitions per line, in all lines
   int BA;                 // augmented width: roundup4(B + 3)
   int n_ct;               // pixel kernel column tiles
+  int n_lines, n_items, n_blocks;  // lines; statistics items; pixel CTAs
   uint32_t flags;
-  int n_iter;
-  float lambda, eps;
+  float eps;
+  const LineInfo* lines;  // device, n_lines
   // caller buffers
   const float* cube;
   const float* k;
@@ -78,9 +99,48 @@ __host__ __device__ inline int k1_entries(int BA) {
 }
 __host__ __device__ inline int k3_entries(int B) { return B + 4; }
 
-__device__ __forceinline__ int part_of(const Params& p, int c) { return c / p.G; }
+// partition of column c of line l; its line; its first column; its width
+__device__ __forceinline__ int part_of(const Params& p, int l, int c) { return l * p.Pl + c / p.G; }
+__device__ __forceinline__ int part_line(const Params& p, int part) { return part / p.Pl; }
+__device__ __forceinline__ int part_col0(const Params& p, int part) { return (part % p.Pl) * p.G; }
 __device__ __forceinline__ int part_ncols(const Params& p, int part) {
-  return min(p.G, p.cols - part * p.G);
+  return min(p.G, p.cols - part_col0(p, part));
+}
+// line of statistics item w / pixel CTA b (binary search over item0 / blk0)
+__device__ __forceinline__ int line_of_item(const Params& p, int w) {
+  int lo = 0, hi = p.n_lines - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.lines[mid].item0 <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int line_of_block(const Params& p, int b) {
+  int lo = 0, hi = p.n_lines - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.lines[mid].blk0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+// statistics item w: line, column, chunk and its rows [r_beg, r_end)
+struct StatItem {
+  int line, c, chunk, r_beg, r_end;
+  long long unit;  // moment unit
+};
+__device__ __forceinline__ StatItem stat_item(const Params& p, int w) {
+  StatItem it;
+  it.line = line_of_item(p, w);
+  const LineInfo L = p.lines[it.line];
+  const int local = w - L.item0;
+  it.chunk = local / p.cols;
+  it.c = local - it.chunk * p.cols;
+  it.r_beg = L.row0 + it.chunk * L.sc_rows;
+  it.r_end = min(L.row0 + L.rows, it.r_beg + L.sc_rows);
+  it.unit = L.k1u0 + (long long)it.c * L.n_sc + it.chunk;
+  return it;
 }
 
 __device__ __forceinline__ const float* pixel_ptr(const Params& p, int row, int col) {
@@ -120,18 +180,20 @@ size_t solve_literal_smem_bytes(int B, int BA);
 cudaError_t stats_set_attributes(int nj, size_t smem);
 cudaError_t pixel_set_attributes(int nj, size_t smem);
 cudaError_t solve_set_attributes(size_t s_init, size_t s_iter, size_t s_lit);
+// `pass`: 0 for the initial statistics / pixel pass, k for iteration k (lines
+// with fewer iterations skip it)
 void stats_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
-                  const Params& p, int mode);
+                  const Params& p, int mode, int pass);
 void pixel_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
-                  const Params& p, int mode, int accumulate);
+                  const Params& p, int mode, int accumulate, int pass);
 void solve_init_launch(size_t smem, cudaStream_t s, const Params& p);
-void solve_iter_launch(size_t smem, cudaStream_t s, const Params& p, int mode);
-void solve_literal_launch(size_t smem, cudaStream_t s, const Params& p);
+void solve_iter_launch(size_t smem, cudaStream_t s, const Params& p, int mode, int pass);
+void solve_literal_launch(size_t smem, cudaStream_t s, const Params& p, int pass);
 size_t stats_tc_smem_bytes(int B);
 bool stats_tc_supported(int B);
 cudaError_t stats_tc_set_attributes(int nj, size_t smem);
 void stats_tc_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
-                     const Params& p, int mode);
+                     const Params& p, int mode, int pass);
 void pilot_launch(cudaStream_t s, const Params& p);
 size_t background_smem_bytes(int B, int BA);
 cudaError_t background_set_attributes(size_t smem);

@@ -135,16 +135,19 @@ extern "C" mf_status mf_background_noalloc(const mf_desc* d, const float* cube,
   p.B = B;
   p.B4 = B / 4;
   p.G = (int)std::min<int64_t>(d->col_group, d->cols);
-  p.P = (p.cols + p.G - 1) / p.G;
+  p.Pl = (p.cols + p.G - 1) / p.G;
+  p.P = p.Pl;
+  p.n_lines = 1;
   p.BA = (B + 6) / 4 * 4;
   p.flags = d->flags;
   p.cube = cube;
   p.mask = mask;
 
-  // scratch layout: pilot (P, B) float | status (P) int | moments
+  // scratch layout: line table (1) | pilot (P, B) float | status (P) int | moments
   const size_t P = (size_t)p.P;
   const size_t K1E = (size_t)mf::k1_entries(p.BA);
-  const size_t fixed = align256(P * B * sizeof(float)) + align256(P * sizeof(int));
+  const size_t line_bytes = align256(sizeof(mf::LineInfo));
+  const size_t fixed = line_bytes + align256(P * B * sizeof(float)) + align256(P * sizeof(int));
   const size_t per_chunk = P * p.G * K1E * sizeof(float2);  // one row chunk per column
   if (fixed + per_chunk > kNoAllocScratchBytes) {
     char msg[256];
@@ -158,8 +161,11 @@ extern "C" mf_status mf_background_noalloc(const mf_desc* d, const float* cube,
   nsc = std::min<long>(nsc, (long)((kNoAllocScratchBytes - fixed) / per_chunk));
   int sc = (int)((p.rows + nsc - 1) / nsc);
   sc = std::max(mf::kStatRows, (sc + mf::kStatRows - 1) / mf::kStatRows * mf::kStatRows);
-  p.sc_rows = sc;
-  p.n_sc = (p.rows + sc - 1) / sc;
+  mf::LineInfo line{};
+  line.rows = p.rows;
+  line.sc_rows = sc;
+  line.n_sc = (p.rows + sc - 1) / sc;
+  p.n_items = p.cols * line.n_sc;
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -167,17 +173,21 @@ extern "C" mf_status mf_background_noalloc(const mf_desc* d, const float* cube,
   unsigned char* base = nullptr;
   mf_status st = setup_device(dev, &base);
   if (st != MF_OK) return st;
-  p.pilot = reinterpret_cast<float*>(base);
-  p.status = reinterpret_cast<int*>(base + align256(P * B * sizeof(float)));
+  p.lines = reinterpret_cast<const mf::LineInfo*>(base);
+  p.pilot = reinterpret_cast<float*>(base + line_bytes);
+  p.status = reinterpret_cast<int*>(base + line_bytes + align256(P * B * sizeof(float)));
   p.k1part = reinterpret_cast<float2*>(base + fixed);
 
   CUtensorMap map;
   if (!encode_map(&map, p, cube)) return fail(MF_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  e = cudaMemsetAsync(p.status, 0, P * sizeof(int), s);
-  if (e != cudaSuccess) return fail(MF_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  // the line table from the stack: a copy from pageable memory returns once
+  // the data is staged
+  e = cudaMemcpyAsync(base, &line, sizeof line, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p.status, 0, P * sizeof(int), s);
+  if (e != cudaSuccess) return fail(MF_ERR_CUDA, std::string("set-up copies: ") + cudaGetErrorString(e));
   const int nj = nj_bucket(p.B4);
-  mf::stats_launch(nj, p.cols * p.n_sc, mf::stats_smem_bytes(B), s, map, p, mf::STAT_INIT);
+  mf::stats_launch(nj, p.n_items, mf::stats_smem_bytes(B), s, map, p, mf::STAT_INIT, 0);
   mf::background_launch(mf::background_smem_bytes(B, p.BA), s, p, mu0, cov0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MF_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));

@@ -59,13 +59,20 @@ int pixel_ctas_per_sm(int nj) { return pix_ctas_per_sm(nj); }
 
 template <int NJ>
 __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
-    pixel_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode, int accumulate) {
+    pixel_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode, int accumulate,
+                 int pass) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_abort;
   __shared__ int s_failed[kTileCols];
 
-  const int ct = blockIdx.x % p.n_ct;
-  const int rb = blockIdx.x / p.n_ct;
+  const int li = line_of_block(p, blockIdx.x);
+  const LineInfo line = p.lines[li];
+  // iteration pass `pass` of a line whose iterations are done: nothing to do
+  if (mode == PIX_ITER && pass > line.n_iter) return;
+  accumulate = accumulate && pass < line.n_iter;
+  const int local = blockIdx.x - line.blk0;
+  const int ct = local % p.n_ct;
+  const int rb = local / p.n_ct;
   const int c0t = ct * kTileCols;
   const int nc = min(kTileCols, p.cols - c0t);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -78,8 +85,8 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
   float* s_v = s_mu + kTileCols * BP;
   float* s_sc = s_v + kTileCols * BP;
 
-  const int r_beg = rb * p.rb_rows;
-  const int r_end = min(p.rows, r_beg + p.rb_rows);
+  const int r_beg = line.row0 + rb * line.rb_rows;
+  const int r_end = min(line.row0 + line.rows, r_beg + line.rb_rows);
   const int nst = (r_end - r_beg + kStageRows - 1) / kStageRows;
   const uint32_t box_bytes = (uint32_t)(kStageRows * kTileCols * B * sizeof(float));
 
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     const int cc = idx / BP, b = idx % BP;
     float m = 0.f, v = 0.f;
     if (cc < nc && b < B) {
-      const size_t pb = (size_t)part_of(p, c0t + cc) * B + b;
+      const size_t pb = (size_t)part_of(p, li, c0t + cc) * B + b;
       m = p.mu0f[pb];
       v = p.vf[pb];
     }
@@ -119,7 +126,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     float4 sc = make_float4(1.f, 0.f, 0.f, 0.f);
     int failed = 1;
     if (tid < nc) {
-      const int part = part_of(p, c0t + tid);
+      const int part = part_of(p, li, c0t + tid);
       sc = reinterpret_cast<const float4*>(p.pscal)[part];
       failed = p.status[part] != MF_OK;
     }
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
   const bool albedo = (p.flags & MF_ALBEDO) != 0;
   const bool sparse = (p.flags & MF_SPARSE) != 0;
   const bool pna = (p.flags & MF_PENALTY_NO_ALBEDO) != 0;
-  const float lam = p.lambda, eps = p.eps;
+  const float lam = line.lambda, eps = p.eps;
   const bool iter = mode == PIX_ITER;
   const float* ain = iter ? p.alpha : p.alpha_init;
 
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     float al;
     if (!iter) {
       const float a0 = p.alpha_init ? a_cur : (r > 0.f ? pp / (r * q) : 0.f);
-      al = p.n_iter == 0 ? a0 : fmaxf(a0, 0.f);
+      al = line.n_iter == 0 ? a0 : fmaxf(a0, 0.f);
     } else {
       const float w = sparse ? 1.f / (a_cur + eps) : 0.f;
       float pen = lam * w;
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
       // bounded wait for the last copy issued on each buffer before the CTA exits
       for (int q2 = 0; q2 < kPixStages; ++q2)
         if (issued[q2] > 0) mbar_wait(&full[q2], (uint32_t)((issued[q2] - 1) & 1));
-      for (int cc = 0; cc < nc; ++cc) p.status[part_of(p, c0t + cc)] = MF_ERR_TIMEOUT;
+      for (int cc = 0; cc < nc; ++cc) p.status[part_of(p, li, c0t + cc)] = MF_ERR_TIMEOUT;
     }
     return;
   }
@@ -292,10 +299,8 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     float sum = 0.f;
 #pragma unroll
     for (int w = 0; w < kStageRows; ++w) sum += red[((size_t)w * kTileCols + cc) * E3 + j];
-    const int col = c0t + cc;
-    const int part = part_of(p, col);
-    const int unit = (col - part * p.G) * p.n_rb + rb;
-    p.k3part[((size_t)part * p.G * p.n_rb + unit) * K3E + j] = sum;
+    const long long unit = line.k3u0 + (long long)(c0t + cc) * line.n_rb + rb;
+    p.k3part[(size_t)unit * K3E + j] = sum;
   }
 }
 
@@ -312,10 +317,10 @@ cudaError_t pixel_set_attributes(int nj, size_t smem) {
 }
 
 void pixel_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
-                  const Params& p, int mode, int accumulate) {
+                  const Params& p, int mode, int accumulate, int pass) {
 #define MF_CASE(NJ)                                                        \
   case NJ:                                                                 \
-    pixel_kernel<NJ><<<grid, kPixThreads, smem, s>>>(map, p, mode, accumulate); \
+    pixel_kernel<NJ><<<grid, kPixThreads, smem, s>>>(map, p, mode, accumulate, pass); \
     return;
   switch (nj) { MF_NJ_CASES(MF_CASE) }
 #undef MF_CASE

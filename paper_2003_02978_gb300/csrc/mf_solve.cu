@@ -113,8 +113,9 @@ __device__ __forceinline__ void block_rc(int t, int nb, int& bi, int& bj) {
 // BA x BA matrix A; each thread keeps 2 x 8 loads in flight
 __device__ void reduce_k1(const Params& p, int part, const DfMat& A) {
   const int BA = p.BA, K1E = k1_entries(BA), nb = BA / 4;
-  const int nunits = part_ncols(p, part) * p.n_sc;
-  const float2* P0 = p.k1part + (size_t)part * p.G * p.n_sc * K1E;
+  const LineInfo& line = p.lines[part_line(p, part)];
+  const int nunits = part_ncols(p, part) * line.n_sc;
+  const float2* P0 = p.k1part + (size_t)(line.k1u0 + (long long)part_col0(p, part) * line.n_sc) * K1E;
   constexpr int kU = 8;
   for (int q0 = threadIdx.x; q0 < K1E; q0 += 2 * kThreads) {
     df sum[2] = {df{0.f, 0.f}, df{0.f, 0.f}};
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode) {
+__global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode, int pass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df s_y[3];
   __shared__ int s_bad;
@@ -446,6 +447,7 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
   const int B = p.B;
   const size_t pb = (size_t)part * B;
   if (p.status[part] != MF_OK) return;
+  if (pass > p.lines[part_line(p, part)].n_iter) return;  // the line's iterations are done
   df* X = reinterpret_cast<df*>(smem_raw);  // L^{-1}, B x B
   df* mom = X + (size_t)B * B;              // B + 3 moments (padded to B + 8)
   df* U0 = mom + B + 8;                     // g
@@ -461,8 +463,9 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
   df* vv = vmk + B;
 
   const int K3E = k3_entries(B);
-  const int nunits = part_ncols(p, part) * p.n_rb;
-  const float* P0 = p.k3part + (size_t)part * p.G * p.n_rb * K3E;
+  const LineInfo& line = p.lines[part_line(p, part)];
+  const int nunits = part_ncols(p, part) * line.n_rb;
+  const float* P0 = p.k3part + (size_t)(line.k3u0 + (long long)part_col0(p, part) * line.n_rb) * K3E;
   for (int t = tid; t < B + 3; t += kThreads) {
     df s{0.f, 0.f};
     for (int u = 0; u < nunits; ++u) s = df_addf(s, P0[(size_t)u * K3E + t]);
@@ -654,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
   }
 }
 
-__global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p) {
+__global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p, int pass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df red[kWarps];
   const int part = blockIdx.x;
@@ -662,6 +665,7 @@ __global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p) {
   const int B = p.B, BA = p.BA;
   const size_t pb = (size_t)part * B;
   if (p.status[part] != MF_OK) return;
+  if (pass > p.lines[part_line(p, part)].n_iter) return;  // the line's iterations are done
   const DfMat A{reinterpret_cast<float*>(smem_raw), BA, BA * BA};
   df* u1 = reinterpret_cast<df*>(smem_raw) + (size_t)BA * BA;  // mu0f
   df* u2 = u1 + B;               // t^k
@@ -768,11 +772,11 @@ cudaError_t solve_set_attributes(size_t s_init, size_t s_iter, size_t s_lit) {
 void solve_init_launch(size_t smem, cudaStream_t s, const Params& p) {
   solve_init_kernel<<<p.P, kThreads, smem, s>>>(p);
 }
-void solve_iter_launch(size_t smem, cudaStream_t s, const Params& p, int mode) {
-  solve_iter_kernel<<<p.P, kThreads, smem, s>>>(p, mode);
+void solve_iter_launch(size_t smem, cudaStream_t s, const Params& p, int mode, int pass) {
+  solve_iter_kernel<<<p.P, kThreads, smem, s>>>(p, mode, pass);
 }
-void solve_literal_launch(size_t smem, cudaStream_t s, const Params& p) {
-  solve_literal_kernel<<<p.P, kThreads, smem, s>>>(p);
+void solve_literal_launch(size_t smem, cudaStream_t s, const Params& p, int pass) {
+  solve_literal_kernel<<<p.P, kThreads, smem, s>>>(p, pass);
 }
 
 }  // namespace mf

@@ -56,16 +56,20 @@ size_t stats_smem_bytes(int B) { return stat_layout(B).total + 128; }
 
 template <int NJ>
 __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__ CUtensorMap map,
-                                                         Params p, int mode) {
+                                                         Params p, int mode, int pass) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(16) float s_ref[kMaxB];
   __shared__ float s_inv_ref2;
   __shared__ int s_pilot, s_abort;
 
-  const int c = blockIdx.x % p.cols;
-  const int chunk = blockIdx.x / p.cols;
-  const int part = part_of(p, c);
-  const int c0 = part * p.G;
+  const StatItem it = stat_item(p, blockIdx.x);
+  const LineInfo line = p.lines[it.line];
+  // literal schedule: lines whose iterations are done take no part
+  if (mode == STAT_LITERAL && pass > line.n_iter) return;
+  const int c = it.c;
+  const int chunk = it.chunk;
+  const int part = part_of(p, it.line, c);
+  const int c0 = part_col0(p, part);
   const int ncp = part_ncols(p, part);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int B = p.B, B4 = p.B4, BA = p.BA;
@@ -76,8 +80,8 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
                      reinterpret_cast<float4*>(smem_raw + L.coef_off) + kStatRows};
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bar_off);
 
-  const int r_beg = chunk * p.sc_rows;
-  const int r_end = min(p.rows, r_beg + p.sc_rows);
+  const int r_beg = it.r_beg;
+  const int r_end = it.r_end;
   const int nst = (r_end - r_beg + kStatRows - 1) / kStatRows;
   const uint32_t box_bytes = (uint32_t)(kStatRows * B * sizeof(float));
 
@@ -101,14 +105,14 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
   // ---- reference direction m
   if (mode == STAT_INIT) {
     if (warp == 0) {
-      // first valid pixel of the partition in row-major order
+      // first valid pixel of the partition (its line's rows) in row-major order
       long found = -1;
-      const long total = (long)p.rows * ncp;
+      const long total = (long)line.rows * ncp;
       for (long base = 0; base < total && found < 0; base += 32) {
         const long i = base + lane;
         bool ok = false;
         if (i < total) {
-          const int row = (int)(i / ncp), col = c0 + (int)(i % ncp);
+          const int row = line.row0 + (int)(i / ncp), col = c0 + (int)(i % ncp);
           ok = !p.mask || p.mask[(size_t)row * p.cols + col] == 0;
           if (ok) {
             const float4* px = reinterpret_cast<const float4*>(pixel_ptr(p, row, col));
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
     const int pi = s_pilot;
     for (int b = tid; b < B; b += kThreads) {
       float v = 0.f;
-      if (pi >= 0) v = pixel_ptr(p, pi / ncp, c0 + pi % ncp)[b];
+      if (pi >= 0) v = pixel_ptr(p, line.row0 + pi / ncp, c0 + pi % ncp)[b];
       s_ref[b] = v;
       if (c == c0 && chunk == 0) p.pilot[(size_t)part * B + b] = v;
     }
@@ -250,8 +254,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
 
   // ---- publish this CTA's moments (double-float pairs)
   const int K1E = k1_entries(BA);
-  const int unit = (c - c0) * p.n_sc + chunk;
-  float2* dst = p.k1part + ((size_t)part * p.G * p.n_sc + unit) * K1E;
+  float2* dst = p.k1part + (size_t)it.unit * K1E;
   for (int q = tid; q < nblk * 16; q += kThreads) {
     const int blk = q >> 4, w = q & 15;
     dst[q] = make_float2(accs[w * nblk + blk], accs[(16 + w) * nblk + blk]);
@@ -271,10 +274,10 @@ cudaError_t stats_set_attributes(int nj, size_t smem) {
 }
 
 void stats_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
-                  const Params& p, int mode) {
-#define MF_CASE(NJ)                                                   \
-  case NJ:                                                            \
-    stats_kernel<NJ><<<grid, kThreads, smem, s>>>(map, p, mode);      \
+                  const Params& p, int mode, int pass) {
+#define MF_CASE(NJ)                                                     \
+  case NJ:                                                              \
+    stats_kernel<NJ><<<grid, kThreads, smem, s>>>(map, p, mode, pass);  \
     return;
   switch (nj) { MF_NJ_CASES(MF_CASE) }
 #undef MF_CASE

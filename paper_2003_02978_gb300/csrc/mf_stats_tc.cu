@@ -142,15 +142,16 @@ __global__ void pilot_kernel(Params p) {
   const int part = blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (part >= p.P) return;
-  const int c0 = part * p.G, ncp = part_ncols(p, part);
-  const long total = (long)p.rows * ncp;
+  const LineInfo line = p.lines[part_line(p, part)];
+  const int c0 = part_col0(p, part), ncp = part_ncols(p, part);
+  const long total = (long)line.rows * ncp;
   float sum[kMaxB / 32] = {};  // bands lane + 32 q
   int n = 0;                   // warp-uniform
   for (long base = 0; base < total && n < kPilot; base += 32) {
     const long i = base + lane;
     bool ok = false;
     if (i < total) {
-      const int row = (int)(i / ncp), col = c0 + (int)(i % ncp);
+      const int row = line.row0 + (int)(i / ncp), col = c0 + (int)(i % ncp);
       ok = !p.mask || p.mask[(size_t)row * p.cols + col] == 0;
       if (ok) {
         const float4* px = reinterpret_cast<const float4*>(pixel_ptr(p, row, col));
@@ -161,7 +162,7 @@ __global__ void pilot_kernel(Params p) {
     while (bal && n < kPilot) {
       const long v = base + __ffs(bal) - 1;
       bal &= bal - 1;
-      const float* px = pixel_ptr(p, (int)(v / ncp), c0 + (int)(v % ncp));
+      const float* px = pixel_ptr(p, line.row0 + (int)(v / ncp), c0 + (int)(v % ncp));
 #pragma unroll
       for (int q = 0; q < kMaxB / 32; ++q)
         if (lane + 32 * q < p.B) sum[q] += px[lane + 32 * q];
@@ -179,7 +180,7 @@ __device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 1, 256;" :::
 
 template <int NJ>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    stats_tc_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode) {
+    stats_tc_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode, int pass) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int s_abort;
 
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* acc_empty = bars + 14; // [2] accumulator drained by the epilogue warps
   uint64_t* drain = bars + 16;     // abort path: every issued MMA completed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + L.slot_off);
-  const int nitems = p.cols * p.n_sc;
+  const int nitems = p.n_items;
   const uint32_t box_bytes = (uint32_t)(kTcRows * B * sizeof(float));
 
   if (tid == 0) {
@@ -228,12 +229,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  auto item_geom = [&](int w, int& c, int& chunk, int& r_beg, int& r_end, int& nst) {
-    c = w % p.cols;
-    chunk = w / p.cols;
-    r_beg = chunk * p.sc_rows;
-    r_end = min(p.rows, r_beg + p.sc_rows);
-    nst = (r_end - r_beg + kTcRows - 1) / kTcRows;
+  // every role walks the same items and stages; an item of a line whose
+  // iterations are done (literal schedule) has no stages
+  auto item_geom = [&](int w, StatItem& it, int& nst) {
+    it = stat_item(p, w);
+    nst = (it.r_end - it.r_beg + kTcRows - 1) / kTcRows;
+    if (mode == STAT_LITERAL && pass > p.lines[it.line].n_iter) nst = 0;
   };
   bool failed = false;
   int issued[kMaxFpStages] = {0, 0, 0};  // producer: copies per float32 stage
@@ -244,8 +245,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       prefetch_tmap(&map);
       int g = 0;
       for (int w = blockIdx.x; w < nitems && !failed; w += gridDim.x) {
-        int c, chunk, r_beg, r_end, nst;
-        item_geom(w, c, chunk, r_beg, r_end, nst);
+        StatItem it;
+        int nst;
+        item_geom(w, it, nst);
         for (int s = 0; s < nst; ++s, ++g) {
           const int fb = g % NF;
           if (!mbar_wait(&fp_empty[fb], (uint32_t)(((g / NF) & 1) ^ 1))) {
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
           }
           mbar_arrive_expect_tx(&fp_full[fb], box_bytes);
-          tma_load_3d(stage(fb), &map, p.band_lo, c, r_beg + s * kTcRows, &fp_full[fb]);
+          tma_load_3d(stage(fb), &map, p.band_lo, it.c, it.r_beg + s * kTcRows, &fp_full[fb]);
           ++issued[fb];
         }
       }
@@ -267,8 +269,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t ops_s = smem_u32(ops);
       int g = 0;
       for (int w = blockIdx.x; w < nitems && !failed; w += gridDim.x) {
-        int c, chunk, r_beg, r_end, nst;
-        item_geom(w, c, chunk, r_beg, r_end, nst);
+        StatItem it;
+        int nst;
+        item_geom(w, it, nst);
         for (int s = 0; s < nst; ++s, ++g) {
           const int sb = g & 1;  // operand set and accumulator of this stage
           if (!mbar_wait(&acc_empty[sb], (uint32_t)(((g >> 1) & 1) ^ 1)) ||
@@ -312,13 +315,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t qsum = tmem + lanes + (uint32_t)(2 * L.accw);
     int g = 0;
     for (int w = blockIdx.x; w < nitems && !failed; w += gridDim.x) {
-      int c, chunk, r_beg, r_end, nst;
-      item_geom(w, c, chunk, r_beg, r_end, nst);
-      const int part = part_of(p, c);
-      const int unit = (c - part * p.G) * p.n_sc + chunk;
+      StatItem it;
+      int nst;
+      item_geom(w, it, nst);
       // entry (a, b) of G = Q_ab + Q_ba: row m of Q gives the first term of
       // the entries (m, j >= m's block) and the second of (j, m)
-      float* dst = reinterpret_cast<float*>(p.k1part + ((size_t)part * p.G * p.n_sc + unit) * K1E);
+      float* dst = reinterpret_cast<float*>(p.k1part + (size_t)it.unit * K1E);
       for (int s = 0; s < nst; ++s, ++g) {
         const int sb = g & 1;
         // warp-uniform decision: tcgen05.ld below needs every lane
@@ -369,8 +371,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const bool albedo = (p.flags & MF_ALBEDO) != 0;
     // (item, stage) after (w, s) in this CTA's sequence, for the prefetch
     auto next_of = [&](int& w, int& s) {
-      int c, chunk, r_beg, r_end, nst;
-      item_geom(w, c, chunk, r_beg, r_end, nst);
+      StatItem it;
+      int nst;
+      item_geom(w, it, nst);
       if (++s >= nst) {
         s = 0;
         w += gridDim.x;
@@ -380,11 +383,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       m_out = 0;
       a_out = 0.f;
       if (w >= nitems) return;
-      int c, chunk, r_beg, r_end, nst;
-      item_geom(w, c, chunk, r_beg, r_end, nst);
-      const int row = r_beg + s * kTcRows + slot;
-      if (row < r_end) {
-        const size_t pix = (size_t)row * p.cols + c;
+      StatItem it;
+      int nst;
+      item_geom(w, it, nst);
+      const int row = it.r_beg + s * kTcRows + slot;
+      if (row < it.r_end) {
+        const size_t pix = (size_t)row * p.cols + it.c;
         if (p.mask) m_out = p.mask[pix];
         if (mode == STAT_LITERAL) a_out = p.alpha[pix];
       }
@@ -400,16 +404,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const float* refsrc = (mode == STAT_INIT ? p.pilot : p.mu0f);
     auto ref_of = [&](int w) -> float {
       if (w >= nitems || tid >= B) return 0.f;
-      return refsrc[(size_t)part_of(p, w % p.cols) * B + tid];
+      const StatItem iw = stat_item(p, w);
+      return refsrc[(size_t)part_of(p, iw.line, iw.c) * B + tid];
     };
     if (tid < B) s_ref[tid] = ref_of(blockIdx.x);
     conv_bar();
     // every converter warp walks every item (and reaches every named barrier)
     // even after a failed wait; it only skips the work
     for (int w = blockIdx.x; w < nitems; w += gridDim.x, ++t) {
-      int c, chunk, r_beg, r_end, nst;
-      item_geom(w, c, chunk, r_beg, r_end, nst);
-      const int part = part_of(p, c);
+      StatItem it;
+      int nst;
+      item_geom(w, it, nst);
+      const int part = part_of(p, it.line, it.c);
       float* ref = s_ref + (t & 1) * (kMaxB + 4);
       const float ref_next = ref_of(w + gridDim.x);
       float inv_ref2;
@@ -432,8 +438,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           continue;
         }
         const int fb = g % NF, sb = g & 1;
-        const int row = r_beg + s * kTcRows + slot;
-        const bool inb = row < r_end;
+        const int row = it.r_beg + s * kTcRows + slot;
+        const bool inb = row < it.r_end;
         // warp-uniform decision: the shuffles below need every lane
         const bool ok_w = mbar_wait(&fp_full[fb], (uint32_t)((g / NF) & 1)) &&
                           mbar_wait(&op_empty[sb], (uint32_t)(((g >> 1) & 1) ^ 1));
@@ -491,7 +497,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_wait(drain, 0);
     }
     if (tid == 0)
-      for (int w = blockIdx.x; w < nitems; w += gridDim.x) p.status[part_of(p, w % p.cols)] = MF_ERR_TIMEOUT;
+      for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const StatItem iw = stat_item(p, w);
+        p.status[part_of(p, iw.line, iw.c)] = MF_ERR_TIMEOUT;
+      }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -516,10 +525,10 @@ void pilot_launch(cudaStream_t s, const Params& p) {
 }
 
 void stats_tc_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
-                     const Params& p, int mode) {
-#define MF_CASE(NJ)                                                           \
-  case NJ:                                                                    \
-    stats_tc_kernel<NJ><<<grid, kTcThreads, smem, s>>>(map, p, mode);         \
+                     const Params& p, int mode, int pass) {
+#define MF_CASE(NJ)                                                             \
+  case NJ:                                                                      \
+    stats_tc_kernel<NJ><<<grid, kTcThreads, smem, s>>>(map, p, mode, pass);     \
     return;
   switch (nj) { MF_NJ_CASES(MF_CASE) }
 #undef MF_CASE

@@ -64,6 +64,20 @@ def test_descriptor_validation(lib, kw, code):
     assert lib.mf_last_error()
 
 
+def test_batched_plan_validation(lib):
+    from paper_2003_02978_gb300._native import MfDesc
+    h = ctypes.c_void_p()
+    rows = (ctypes.c_int64 * 3)(100, 200, 300)
+    assert lib.mf_plan_batched(ctypes.byref(_desc(rows=601)), rows, 3, ctypes.byref(h)) == 1
+    assert b"sum of the line rows" in lib.mf_last_error()
+    bad = (ctypes.c_int64 * 3)(100, -5, 505)
+    assert lib.mf_plan_batched(ctypes.byref(_desc(rows=600)), bad, 3, ctypes.byref(h)) == 1
+    assert lib.mf_plan_batched(ctypes.byref(_desc(rows=600)), rows, 0, ctypes.byref(h)) == 1
+    assert lib.mf_plan_batched(ctypes.byref(_desc(rows=600)), None, 3, ctypes.byref(h)) == 1
+    assert lib.mf_num_lines(None) == -1
+    assert lib.mf_retrieve_batched(None, None, None, None, 1e-9, None, None, None, None) == 1
+
+
 def test_null_arguments(lib):
     assert lib.mf_plan(None, None) == 1
     assert lib.mf_retrieve(None, None, None, 1.0, 1.0, 1, None, None, None, None, None) == 1
