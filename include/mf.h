@@ -133,6 +133,27 @@ mf_status mf_retrieve_host(mf_plan_t plan, const float* cube, const float* k, do
 mf_status mf_plan_batched(const mf_desc* desc, const int64_t* line_rows, int32_t n_lines,
                           mf_plan_t* out);
 
+/* Launch-shape choices of a plan (0 = the library's default, which sizes the
+ * grids from the SM count):
+ *   pixel_rows  rows per pixel-kernel CTA (rounded up to 8; per line, the
+ *               line is split evenly into blocks of at most this many rows)
+ *   stat_rows   rows per statistics work item (rounded up to 128; the
+ *               BF16-split form accepts at most 1024 before its stated bound
+ *               is untested)
+ *   use_graph   < 0: launch the kernels directly instead of replaying a CUDA
+ *               graph of the retrieval */
+typedef struct {
+  int32_t pixel_rows;
+  int32_t stat_rows;
+  int32_t use_graph;
+} mf_tuning;
+
+/* mf_plan / mf_plan_batched with launch-shape choices (an autotuner's
+ * output); line_rows NULL means one line of desc->rows.  tuning may be
+ * NULL. */
+mf_status mf_plan_ex(const mf_desc* desc, const int64_t* line_rows, int32_t n_lines,
+                     const mf_tuning* tuning, mf_plan_t* out);
+
 /* Number of lines of a plan (1 for mf_plan), or -1 for a null plan. */
 int32_t mf_num_lines(mf_plan_t plan);
 

@@ -13,7 +13,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from ._native import MfDesc, MFError, check, lib
+from ._native import MfDesc, MFError, MfTuning, check, lib
 
 ALBEDO = 1
 SPARSE = 2
@@ -46,6 +46,12 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _tuning(t) -> MfTuning:
+    """mf_tuning from a dict {pixel_rows, stat_rows, use_graph} (0 = default)."""
+    return MfTuning(pixel_rows=int(t.get("pixel_rows", 0)), stat_rows=int(t.get("stat_rows", 0)),
+                    use_graph=int(t.get("use_graph", 0)))
+
+
 def _stream_handle(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -68,7 +74,7 @@ class Plan:
     once, on the current CUDA device).  ``retrieve`` allocates nothing."""
 
     def __init__(self, rows, cols, bands_total, band_lo=0, band_hi=None, col_group=1,
-                 flags=DEFAULT_FLAGS, precision=FP32):
+                 flags=DEFAULT_FLAGS, precision=FP32, tuning=None):
         band_hi = bands_total if band_hi is None else band_hi
         self.shape = Shape(int(rows), int(cols), int(bands_total), int(band_lo), int(band_hi),
                            int(col_group), int(flags), int(precision))
@@ -76,7 +82,13 @@ class Plan:
                    band_hi=band_hi, col_group=col_group, layout=0, precision=precision,
                    flags=flags)
         h = ctypes.c_void_p()
-        check(lib().mf_plan(ctypes.byref(d), ctypes.byref(h)), "mf_plan")
+        if tuning is None:
+            check(lib().mf_plan(ctypes.byref(d), ctypes.byref(h)), "mf_plan")
+        else:
+            t = _tuning(tuning)
+            check(lib().mf_plan_ex(ctypes.byref(d), None, 1, ctypes.byref(t), ctypes.byref(h)),
+                  "mf_plan_ex")
+        self.tuning = tuning
         self._h = h
         self.B = band_hi - band_lo
         self.P = int(lib().mf_num_partitions(h))
@@ -168,7 +180,7 @@ class BatchPlan(Plan):
     every line, each with its own partitions, lambda and iteration count."""
 
     def __init__(self, line_rows, cols, bands_total, band_lo=0, band_hi=None, col_group=1,
-                 flags=DEFAULT_FLAGS, precision=FP32):
+                 flags=DEFAULT_FLAGS, precision=FP32, tuning=None):
         line_rows = [int(r) for r in line_rows]
         band_hi = bands_total if band_hi is None else band_hi
         rows = sum(line_rows)
@@ -179,8 +191,10 @@ class BatchPlan(Plan):
                    flags=flags)
         lr = (ctypes.c_int64 * len(line_rows))(*line_rows)
         h = ctypes.c_void_p()
-        check(lib().mf_plan_batched(ctypes.byref(d), lr, len(line_rows), ctypes.byref(h)),
-              "mf_plan_batched")
+        t = _tuning(tuning or {})
+        check(lib().mf_plan_ex(ctypes.byref(d), lr, len(line_rows), ctypes.byref(t),
+                               ctypes.byref(h)), "mf_plan_ex")
+        self.tuning = tuning
         self._h = h
         self.line_rows = line_rows
         self.n_lines = int(lib().mf_num_lines(h))

@@ -14,6 +14,10 @@ STATUS_NAMES = {0: "MF_OK", 1: "MF_ERR_INVALID_ARG", 2: "MF_ERR_CUDA", 3: "MF_ER
                 7: "MF_ERR_INTERNAL", 8: "MF_ERR_UNSUPPORTED"}
 
 
+class MfTuning(ctypes.Structure):
+    _fields_ = [("pixel_rows", c_int32), ("stat_rows", c_int32), ("use_graph", c_int32)]
+
+
 class MfDesc(ctypes.Structure):
     _fields_ = [("rows", c_int64), ("cols", c_int64), ("bands_total", c_int64),
                 ("band_lo", c_int32), ("band_hi", c_int32), ("col_group", c_int32),
@@ -58,6 +62,9 @@ def lib() -> ctypes.CDLL:
     L.mf_background_noalloc.restype = c_int
     L.mf_plan_batched.argtypes = [POINTER(MfDesc), POINTER(c_int64), c_int32, POINTER(c_void_p)]
     L.mf_plan_batched.restype = c_int
+    L.mf_plan_ex.argtypes = [POINTER(MfDesc), POINTER(c_int64), c_int32, POINTER(MfTuning),
+                             POINTER(c_void_p)]
+    L.mf_plan_ex.restype = c_int
     L.mf_num_lines.argtypes = [c_void_p]
     L.mf_num_lines.restype = c_int32
     L.mf_retrieve_batched.argtypes = [c_void_p, fp, fp, POINTER(c_double), c_double,

@@ -65,6 +65,23 @@ struct mf_plan_s {
   mf::LineInfo* lines_pinned = nullptr;
   cudaEvent_t lines_copied = nullptr;
   bool lines_valid = false;
+  // CUDA graph of the whole retrieval (re-captured when a pointer, the pass
+  // count or eps changes); captured on a plan-owned stream, launched on the
+  // caller's
+  struct GraphKey {
+    const void* ptr[6];
+    int n_iter;
+    float eps;
+    bool operator==(const GraphKey& o) const {
+      for (int i = 0; i < 6; ++i)
+        if (ptr[i] != o.ptr[i]) return false;
+      return n_iter == o.n_iter && eps == o.eps;
+    }
+  };
+  bool use_graph = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  GraphKey gkey{};
   // tensor maps of the last cube pointer (re-encoded when it changes)
   const float* map_cube = nullptr;
   CUtensorMap map_stats{}, map_pixel{};
@@ -233,7 +250,8 @@ namespace {
 
 // Validate the descriptor and build a plan over n_lines flightlines stacked
 // along rows (line_rows[l] rows each; d->rows is their sum).
-mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines, mf_plan_t* out) {
+mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
+                     const mf_tuning* tune, mf_plan_t* out) {
   if (!d || !out) return fail(MF_ERR_INVALID_ARG, "null descriptor or output");
   *out = nullptr;
   if (d->rows <= 0 || d->cols <= 0 || d->bands_total <= 0)
@@ -285,6 +303,8 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines, mf
   p.flags = d->flags;
   p.n_lines = n_lines;
   pl->nj = nj_bucket(p.B4);
+  pl->use_graph = env_int("MF_GRAPH", 1) != 0;
+  if (tune && tune->use_graph < 0) pl->use_graph = false;
 
   cudaError_t e = cudaGetDevice(&pl->device);
   if (e == cudaSuccess)
@@ -301,14 +321,14 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines, mf
   // 1024 rows in the tensor-core form (float32 sums in tensor memory) and
   // 2048 otherwise.  Every line is split evenly into whole blocks / chunks.
   p.n_ct = (p.cols + mf::kTileCols - 1) / mf::kTileCols;
-  int hp = env_int("MF_RB_ROWS", 0);
+  int hp = tune && tune->pixel_rows > 0 ? tune->pixel_rows : env_int("MF_RB_ROWS", 0);
   if (hp <= 0) {
     const long waves = (long)mf::pixel_ctas_per_sm(pl->nj) * pl->num_sms;
     const long nrb = std::max<long>(1, (waves + p.n_ct - 1) / p.n_ct);
     hp = (int)std::min<long>(512, (p.rows + nrb - 1) / nrb);
   }
   hp = std::max(hp, mf::kStageRows);
-  int hs = env_int("MF_SC_ROWS", 0);
+  int hs = tune && tune->stat_rows > 0 ? tune->stat_rows : env_int("MF_SC_ROWS", 0);
   if (hs <= 0) {
     const long target_ctas = 2400;
     const long nsc = std::max<long>(1, (target_ctas + p.cols - 1) / p.cols);
@@ -460,21 +480,53 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
     }
     pl->map_cube = cube;
   }
-  MF_CUDA(cudaMemsetAsync(p.status, 0, (size_t)p.P * sizeof(int), s));
-  stats_dispatch(pl, p, mf::STAT_INIT, 0, s);
-  solve_init_dispatch(pl, p, s);
-  pixel_dispatch(pl, p, mf::PIX_INIT, n_iter_max > 0, 0, s);
-  for (int it = 1; it <= n_iter_max; ++it) {
-    if (literal) {
-      solve_iter_dispatch(pl, p, mf::SOLVE_MEAN_ONLY, it, s);
-      stats_dispatch(pl, p, mf::STAT_LITERAL, it, s);
-      solve_literal_dispatch(pl, p, it, s);
-    } else {
-      solve_iter_dispatch(pl, p, mf::SOLVE_FUSED, it, s);
+  auto enqueue = [&](cudaStream_t q) {
+    cudaMemsetAsync(p.status, 0, (size_t)p.P * sizeof(int), q);
+    stats_dispatch(pl, p, mf::STAT_INIT, 0, q);
+    solve_init_dispatch(pl, p, q);
+    pixel_dispatch(pl, p, mf::PIX_INIT, n_iter_max > 0, 0, q);
+    for (int it = 1; it <= n_iter_max; ++it) {
+      if (literal) {
+        solve_iter_dispatch(pl, p, mf::SOLVE_MEAN_ONLY, it, q);
+        stats_dispatch(pl, p, mf::STAT_LITERAL, it, q);
+        solve_literal_dispatch(pl, p, it, q);
+      } else {
+        solve_iter_dispatch(pl, p, mf::SOLVE_FUSED, it, q);
+      }
+      pixel_dispatch(pl, p, mf::PIX_ITER, it < n_iter_max, it, q);
     }
-    pixel_dispatch(pl, p, mf::PIX_ITER, it < n_iter_max, it, s);
+  };
+  // direct launches when profiling (events per kernel) or when the caller is
+  // capturing its own graph; otherwise one graph launch
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  MF_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (pl->profile || !pl->use_graph || cs != cudaStreamCaptureStatusNone) {
+    enqueue(s);
+    MF_CUDA(cudaGetLastError());
+  } else {
+    const mf_plan_s::GraphKey key{{cube, k, mask, alpha_init, alpha_out, albedo_out},
+                                  n_iter_max, (float)eps};
+    if (!pl->gexec || !(key == pl->gkey)) {
+      if (pl->gexec) {
+        MF_CUDA(cudaGraphExecDestroy(pl->gexec));
+        pl->gexec = nullptr;
+      }
+      if (!pl->cap_stream) MF_CUDA(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      MF_CUDA(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+      enqueue(pl->cap_stream);
+      const cudaError_t e1 = cudaStreamEndCapture(pl->cap_stream, &g);
+      if (e1 != cudaSuccess) return fail(MF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e1));
+      const cudaError_t e2 = cudaGraphInstantiate(&pl->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) {
+        pl->gexec = nullptr;
+        return fail(MF_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e2));
+      }
+      pl->gkey = key;
+    }
+    MF_CUDA(cudaGraphLaunch(pl->gexec, s));
   }
-  MF_CUDA(cudaGetLastError());
   pl->last_stream = s;
   return MF_OK;
 }
@@ -496,14 +548,23 @@ mf_status mf_plan(const mf_desc* d, mf_plan_t* out) {
   g_last_error.clear();
   if (!d || !out) return fail(MF_ERR_INVALID_ARG, "null descriptor or output");
   const int64_t rows = d->rows;
-  return build_plan(d, &rows, 1, out);
+  return build_plan(d, &rows, 1, nullptr, out);
+}
+
+mf_status mf_plan_ex(const mf_desc* d, const int64_t* line_rows, int32_t n_lines,
+                     const mf_tuning* tuning, mf_plan_t* out) {
+  g_last_error.clear();
+  if (!d || !out) return fail(MF_ERR_INVALID_ARG, "null descriptor or output");
+  const int64_t rows = d->rows;
+  if (!line_rows) return build_plan(d, &rows, 1, tuning, out);
+  return build_plan(d, line_rows, n_lines, tuning, out);
 }
 
 mf_status mf_plan_batched(const mf_desc* d, const int64_t* line_rows, int32_t n_lines,
                           mf_plan_t* out) {
   g_last_error.clear();
   if (!line_rows) return fail(MF_ERR_INVALID_ARG, "null line_rows");
-  return build_plan(d, line_rows, n_lines, out);
+  return build_plan(d, line_rows, n_lines, nullptr, out);
 }
 
 int32_t mf_num_lines(mf_plan_t pl) { return pl ? pl->n_lines : -1; }
@@ -522,6 +583,8 @@ void mf_destroy(mf_plan_t pl) {
   cudaFree(pl->h_alpha);
   if (pl->lines_pinned) cudaFreeHost(pl->lines_pinned);
   if (pl->lines_copied) cudaEventDestroy(pl->lines_copied);
+  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   delete pl;
 }
 

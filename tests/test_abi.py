@@ -75,6 +75,8 @@ def test_batched_plan_validation(lib):
     assert lib.mf_plan_batched(ctypes.byref(_desc(rows=600)), rows, 0, ctypes.byref(h)) == 1
     assert lib.mf_plan_batched(ctypes.byref(_desc(rows=600)), None, 3, ctypes.byref(h)) == 1
     assert lib.mf_num_lines(None) == -1
+    assert lib.mf_plan_ex(None, None, 1, None, ctypes.byref(h)) == 1
+    assert lib.mf_plan_ex(ctypes.byref(_desc(rows=601)), rows, 3, None, ctypes.byref(h)) == 1
     assert lib.mf_retrieve_batched(None, None, None, None, 1e-9, None, None, None, None) == 1
 
 
