@@ -215,6 +215,96 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+BATCH_LINES = 8
+
+
+def batched_form(args, dev, precision):
+    """The batched form on a batch of the batched workload's flightlines
+    (rows uniform in 2000-30000, 598 x 72, per-column masked fraction
+    U(0, 0.3), per-line n_iter in 5..20 and lambda log-uniform in
+    [1e-4, 1e-2]; one shared target spectrum), stacked along rows: Mpixel/s of
+    one batched retrieval (CUDA-graph replay) against the plain FP32 form
+    (literal schedule, one single-line plan per line, in sequence), with the
+    alpha error of both against the FP64 oracle on sampled partitions."""
+    import torch
+    import paper_2003_02978_gb300 as mfg
+    from synth import batched_lines, make_scene
+    lines = batched_lines(BATCH_LINES, seed=11)
+    scenes = [make_scene(ln["rows"], ln["cols"], ln["bands"], n_plumes=20,
+                         plume_sigma=(3.0, 15.0), plume_peak=(500.0, 5000.0),
+                         mask_col_frac=ln["mask_col_frac"], seed=ln["seed"], device=dev,
+                         keep_truth=False) for ln in lines]
+    k = torch.as_tensor(np.asarray(scenes[0].k, np.float32), device=dev)
+    cube = torch.cat([sc.cube for sc in scenes], 0).contiguous()
+    mask = torch.cat([sc.mask for sc in scenes], 0).contiguous()
+    rows = [ln["rows"] for ln in lines]
+    lams = [ln["lam"] for ln in lines]
+    nits = [ln["n_iter"] for ln in lines]
+    npix = cube.shape[0] * cube.shape[1]
+    plan = mfg.BatchPlan(rows, 598, 72, precision=precision)
+    out = torch.empty(cube.shape[:2], dtype=torch.float32, device=dev)
+    for _ in range(2):
+        plan.retrieve(cube, k, lams, 1e-9, nits, mask=mask, out=out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        plan.retrieve(cube, k, lams, 1e-9, nits, mask=mask, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / reps
+    status_ok = bool(np.all(plan.status() == 0))
+    slices = plan.line_slices()
+    plan.close()
+    # plain FP32 form: literal schedule, one plan per line, in sequence
+    plain = [mfg.Plan(r, 598, 72, flags=mfg.ALBEDO | mfg.SPARSE | mfg.LITERAL) for r in rows]
+    outp = torch.empty_like(out)
+    for pl_, sl, lam, n in zip(plain, slices, lams, nits):
+        pl_.retrieve(cube[sl], k, lam, 1e-9, n, mask=mask[sl], out=outp[sl])
+    torch.cuda.synchronize()
+    e0.record()
+    for pl_, sl, lam, n in zip(plain, slices, lams, nits):
+        pl_.retrieve(cube[sl], k, lam, 1e-9, n, mask=mask[sl], out=outp[sl])
+    e1.record()
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    for pl_ in plain:
+        pl_.close()
+    err = None
+    if not args.no_oracle:
+        import oracle
+        err = {}
+        rng = np.random.default_rng(5)
+        for name, a in (("batched", out), ("plain_fp32", outp)):
+            num = den = mx = mref = 0.0
+            for li in (0, BATCH_LINES - 1):
+                cols = np.sort(rng.choice(598, 3, replace=False))
+                sub = cube[slices[li]][:, cols].cpu().numpy()
+                msk = mask[slices[li]][:, cols].cpu().numpy()
+                ref, _ = oracle.retrieve(sub.astype(np.float64),
+                                         np.asarray(k.cpu().numpy(), np.float64),
+                                         lams[li], 1e-9, nits[li], mask=msk)
+                valid = oracle.valid_pixels(sub, msk)
+                g = a[slices[li]][:, cols].cpu().numpy().astype(np.float64)
+                d = (g - ref)[valid]
+                num += float((d * d).sum())
+                den += float((ref[valid] ** 2).sum())
+                mx = max(mx, float(np.abs(d).max()))
+                mref = max(mref, float(np.abs(ref[valid]).max()))
+            err[name] = {"e_inf": mx / mref, "e_2": (num / den) ** 0.5,
+                         "sample": "3 random whole partitions of the first and last line"}
+    del cube, mask, out, outp, scenes
+    torch.cuda.empty_cache()
+    return {"workload": f"{BATCH_LINES} flightlines, rows {rows}, 598 x 72, per-column masked "
+                        "fraction U(0, 0.3), n_iter " + str(nits),
+            "pixels": npix, "precision": "bf16split" if precision else "fp32",
+            "value": npix / (ms_b * 1e-3) / 1e6, "ms_per_batch": ms_b,
+            "plain_fp32_value": npix / (ms_p * 1e-3) / 1e6, "plain_fp32_ms": ms_p,
+            "status_ok": status_ok, "alpha_error": err}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,6 +312,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle checks")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -343,6 +434,10 @@ def main():
     h2d = cube_h.numel() * 4 + mask_h.numel() + k_h.size * 4
     d2h = alpha_h.numel() * 4
 
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = batched_form(args, dev, mfg.BF16SPLIT)
+
     result = {}
     if rank == 0:
         # alpha error against the FP64 oracle on sampled whole partitions, and
@@ -406,6 +501,7 @@ def main():
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "api": "mf_retrieve_host (pinned host buffers)"},
             "cpu_baseline": cpu,
+            "batched": batched,
             "clocks": clocks,
         }
         print(json.dumps(result), flush=True)
