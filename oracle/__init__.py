@@ -8,3 +8,4 @@ from .mf_oracle import (ALBEDO, SPARSE, LITERAL, PENALTY_NO_ALBEDO, NotSPD,  # n
                         retrieve, retrieve_partition, partitions, matched_filter,
                         pixel_energy, near_threshold, valid_pixels,
                         amplification, retrieve_amplification)
+from .mf_grad import retrieve_partition_t, vjp as grad_vjp  # noqa: F401,E402
