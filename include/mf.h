@@ -168,6 +168,37 @@ mf_status mf_retrieve_batched(mf_plan_t plan, const float* cube, const float* k,
                               const double* lambda, double eps, const int32_t* n_iter,
                               const uint8_t* mask, float* alpha_out, void* stream);
 
+/* Differentiation form: a retrieval checkpointed for the backward pass.
+ *
+ * mf_ckpt_bytes: device bytes of a checkpoint for n_iter iterations (alpha^k
+ * of every pass, per partition and pass mu^k, t^k, v^k, g^k, q^k and the
+ * moments of beta, plus every buffer the backward pass needs; with cube_grad
+ * also two coefficients per pixel and pass for the cube gradient).  0 for a
+ * null plan.
+ *
+ * mf_retrieve_train: mf_retrieve (no alpha_init, no albedo output) that also
+ * writes the checkpoint to `ckpt` (device, caller-owned, 256-byte aligned,
+ * mf_ckpt_bytes long).  Single-line plans of the fused schedule only (no
+ * MF_LITERAL; the literal schedule computes the same C^k); otherwise
+ * MF_ERR_UNSUPPORTED.  The cube, k and mask must stay unchanged until the
+ * backward pass.
+ *
+ * mf_retrieve_backward: the adjoint of that retrieval (the unrolled
+ * iterations of Fig. 1 reversed, see mf_backward.cu) for the output adjoint
+ * grad_alpha (device, rows x cols): grad_k (device, B float32, gradient with
+ * respect to the unit absorption spectrum s), grad_lambda (device, 1
+ * float32), grad_cube (device, rows x cols x B float32 over the band
+ * window, or NULL; needs cube_grad at the forward).  Masked and non-finite
+ * pixels and partitions that failed get zero gradient.  The clamp max(., 0)
+ * has subgradient 0 at the kink.  Enqueued on `stream`; allocates nothing. */
+size_t mf_ckpt_bytes(mf_plan_t plan, int32_t n_iter, int32_t cube_grad);
+mf_status mf_retrieve_train(mf_plan_t plan, const float* cube, const float* k, double lambda,
+                            double eps, int32_t n_iter, const uint8_t* mask, float* alpha_out,
+                            void* ckpt, int32_t cube_grad, void* stream);
+mf_status mf_retrieve_backward(mf_plan_t plan, const void* ckpt, const float* grad_alpha,
+                               float* grad_k, float* grad_lambda, float* grad_cube,
+                               void* stream);
+
 /* Background statistics of the last retrieval's initialisation (Fig. 1,
  * initial mean and covariance): mu0 (P, B) and cov0 (P, B, B), float64
  * DEVICE buffers.  Ordered after the retrieval on `stream`; synchronises it

@@ -33,7 +33,7 @@ TABLE_I = {
     "albedo_rwl1mf": (True, ALBEDO | SPARSE),
 }
 
-__all__ = ["Plan", "BatchPlan", "retrieve", "MFError", "ALBEDO", "SPARSE", "LITERAL", "PENALTY_NO_ALBEDO",
+__all__ = ["Plan", "BatchPlan", "Retrieve", "retrieve_differentiable", "retrieve", "MFError", "ALBEDO", "SPARSE", "LITERAL", "PENALTY_NO_ALBEDO",
            "FP32", "BF16SPLIT", "TABLE_I", "library_path"]
 
 
@@ -150,6 +150,48 @@ class Plan:
               "mf_retrieve_host")
         return out
 
+    def ckpt_bytes(self, n_iter, cube_grad=False) -> int:
+        return int(lib().mf_ckpt_bytes(self._h, int(n_iter), int(bool(cube_grad))))
+
+    def retrieve_train(self, cube, k, lam, eps, n_iter, mask=None, cube_grad=False, out=None,
+                       ckpt=None, stream=None):
+        """Checkpointed retrieval for the backward pass.  Returns (alpha,
+        ckpt), ckpt a uint8 CUDA tensor holding the checkpoint (allocated
+        here unless given)."""
+        s = self.shape
+        self._check_cube(cube)
+        k = torch.as_tensor(k, dtype=torch.float32, device=cube.device).contiguous()
+        if ckpt is None:
+            ckpt = torch.empty(self.ckpt_bytes(n_iter, cube_grad) + 256, dtype=torch.uint8,
+                               device=cube.device)
+        off = (-ckpt.data_ptr()) % 256
+        if out is None:
+            out = torch.empty((s.rows, s.cols), dtype=torch.float32, device=cube.device)
+        check(lib().mf_retrieve_train(self._h, _ptr(cube), _ptr(k), float(lam), float(eps),
+                                      int(n_iter), _ptr(mask), _ptr(out),
+                                      ctypes.c_void_p(ckpt.data_ptr() + off),
+                                      int(bool(cube_grad)), _stream_handle(stream)),
+              "mf_retrieve_train")
+        self._train = (k, mask, ckpt, off, bool(cube_grad))
+        return out, ckpt
+
+    def backward(self, ckpt, grad_alpha, cube_grad=False, stream=None):
+        """Adjoint of the last retrieve_train for grad_alpha (rows, cols):
+        (grad_k (B,), grad_lambda (), grad_cube (rows, cols, B) or None)."""
+        s = self.shape
+        k, mask, ck, off, has_cube = self._train
+        assert ck is ckpt, "ckpt must be the one returned by retrieve_train"
+        dev = ck.device
+        g = grad_alpha.to(device=dev, dtype=torch.float32).contiguous()
+        grad_k = torch.empty(self.B, dtype=torch.float32, device=dev)
+        grad_l = torch.empty((), dtype=torch.float32, device=dev)
+        grad_c = torch.empty((s.rows, s.cols, self.B), dtype=torch.float32, device=dev) \
+            if cube_grad else None
+        check(lib().mf_retrieve_backward(self._h, ctypes.c_void_p(ck.data_ptr() + off), _ptr(g),
+                                         _ptr(grad_k), _ptr(grad_l), _ptr(grad_c),
+                                         _stream_handle(stream)), "mf_retrieve_backward")
+        return grad_k, grad_l, grad_c
+
     def status(self) -> np.ndarray:
         st = (ctypes.c_int32 * self.P)()
         lib().mf_plan_status(self._h, st)
@@ -233,6 +275,44 @@ class BatchPlan(Plan):
             out.append(slice(r0, r0 + r))
             r0 += r
         return out
+
+
+class Retrieve(torch.autograd.Function):
+    """alpha = retrieval(cube, k, lam) as a differentiable operation: forward
+    through mf_retrieve_train, backward through mf_retrieve_backward (the
+    hand-written adjoint).  Gradients for cube (band window), k and lam."""
+
+    @staticmethod
+    def forward(ctx, cube, k, lam, plan, eps, n_iter, mask, cube_grad):
+        alpha, ckpt = plan.retrieve_train(cube.detach(), k.detach(), float(lam), eps, n_iter,
+                                          mask=mask, cube_grad=cube_grad)
+        ctx.plan, ctx.ckpt, ctx.cube_grad = plan, ckpt, cube_grad
+        ctx.lam_shape = lam.shape if isinstance(lam, torch.Tensor) else None
+        return alpha
+
+    @staticmethod
+    def backward(ctx, grad_alpha):
+        need_cube = ctx.cube_grad and ctx.needs_input_grad[0]
+        gk, gl, gc = ctx.plan.backward(ctx.ckpt, grad_alpha, cube_grad=need_cube)
+        if gc is not None and gc.shape[-1] != ctx.plan.shape.bands_total:
+            full = torch.zeros((*gc.shape[:2], ctx.plan.shape.bands_total), dtype=gc.dtype,
+                               device=gc.device)
+            full[..., ctx.plan.shape.band_lo:ctx.plan.shape.band_hi] = gc
+            gc = full
+        if ctx.lam_shape is not None:
+            gl = gl.reshape(ctx.lam_shape)
+        return gc, gk, gl, None, None, None, None, None
+
+
+def retrieve_differentiable(cube, k, lam, eps=1e-9, n_iter=10, mask=None, plan=None,
+                            cube_grad=True):
+    """Differentiable retrieval: gradients flow to cube (if cube_grad), k and
+    lam (a tensor) through the library's adjoint."""
+    if plan is None:
+        rows, cols, bt = cube.shape
+        plan = Plan(rows, cols, bt)
+    lam_t = lam if isinstance(lam, torch.Tensor) else torch.tensor(float(lam))
+    return Retrieve.apply(cube, k, lam_t, plan, eps, n_iter, mask, cube_grad)
 
 
 _PLANS: dict = {}

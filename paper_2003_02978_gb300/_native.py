@@ -65,6 +65,13 @@ def lib() -> ctypes.CDLL:
     L.mf_plan_ex.argtypes = [POINTER(MfDesc), POINTER(c_int64), c_int32, POINTER(MfTuning),
                              POINTER(c_void_p)]
     L.mf_plan_ex.restype = c_int
+    L.mf_ckpt_bytes.argtypes = [c_void_p, c_int32, c_int32]
+    L.mf_ckpt_bytes.restype = ctypes.c_size_t
+    L.mf_retrieve_train.argtypes = [c_void_p, fp, fp, c_double, c_double, c_int32, fp, fp, fp,
+                                    c_int32, c_void_p]
+    L.mf_retrieve_train.restype = c_int
+    L.mf_retrieve_backward.argtypes = [c_void_p, fp, fp, fp, fp, fp, c_void_p]
+    L.mf_retrieve_backward.restype = c_int
     L.mf_num_lines.argtypes = [c_void_p]
     L.mf_num_lines.restype = c_int32
     L.mf_retrieve_batched.argtypes = [c_void_p, fp, fp, POINTER(c_double), c_double,

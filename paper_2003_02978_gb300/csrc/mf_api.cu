@@ -78,6 +78,16 @@ struct mf_plan_s {
       return n_iter == o.n_iter && eps == o.eps;
     }
   };
+  // the last checkpointed forward (mf_retrieve_train), for mf_retrieve_backward
+  struct Train {
+    const void* ckpt = nullptr;
+    int n_iter = 0;
+    bool cube_grad = false;
+    const float* cube = nullptr;
+    const float* k = nullptr;
+    const uint8_t* mask = nullptr;
+    double eps = 0.0;
+  } train;
   bool use_graph = true;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -460,7 +470,8 @@ mf_status upload_lines(mf_plan_s* pl, const double* lambda, const int32_t* n_ite
 // later passes inside the kernels).
 mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double eps,
                         int32_t n_iter_max, const uint8_t* mask, const float* alpha_init,
-                        float* alpha_out, float* albedo_out, cudaStream_t s) {
+                        float* alpha_out, float* albedo_out, cudaStream_t s,
+                        const mf::Params* ck = nullptr) {
   if ((reinterpret_cast<uintptr_t>(cube) & 15) != 0)
     return fail(MF_ERR_INVALID_ARG, "cube must be 16-byte aligned");
   mf::Params p = pl->prm;
@@ -471,6 +482,12 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
   p.alpha = alpha_out;
   p.albedo = albedo_out;
   p.eps = (float)eps;
+  if (ck) {
+    p.ck_alpha = ck->ck_alpha;
+    p.ck_vec = ck->ck_vec;
+    p.ck_sc = ck->ck_sc;
+    p.ck_stages = ck->ck_stages;
+  }
   const bool literal = (p.flags & MF_LITERAL) != 0;
   if (cube != pl->map_cube) {
     if (!encode_cube_map(&pl->map_stats, pl->prm, cube, 1, mf::kStatRows) ||
@@ -500,7 +517,7 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
   // capturing its own graph; otherwise one graph launch
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   MF_CUDA(cudaStreamIsCapturing(s, &cs));
-  if (pl->profile || !pl->use_graph || cs != cudaStreamCaptureStatusNone) {
+  if (pl->profile || !pl->use_graph || ck || cs != cudaStreamCaptureStatusNone) {
     enqueue(s);
     MF_CUDA(cudaGetLastError());
   } else {
@@ -623,6 +640,158 @@ mf_status mf_retrieve_batched(mf_plan_t pl, const float* cube, const float* k,
   mf_status st = upload_lines(pl, lambda, n_iter, s);
   if (st != MF_OK) return st;
   return run_retrieval(pl, cube, k, eps, n_max, mask, nullptr, alpha_out, nullptr, s);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Layout of a training checkpoint (caller-owned device memory): the forward's
+// checkpoints and every buffer of the backward pass.
+struct CkLayout {
+  size_t alpha, vec, sc, abar0, abar1, rbar, coef, vkf, zf, bpart, psc, carry, mubar0, sbar,
+      lbar, mu0bar, total;
+};
+CkLayout ck_layout(const mf_plan_s* pl, int n_iter, bool cube_grad) {
+  const mf::Params& p = pl->prm;
+  const size_t P = p.P, B = p.B, S = (size_t)n_iter + 1;
+  const size_t npix = (size_t)p.rows * p.cols;
+  const size_t units = (size_t)p.cols * pl->lines[0].n_rb;
+  CkLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = align_up(off, 256);
+    const size_t at = off;
+    off += bytes;
+    return at;
+  };
+  L.alpha = take(S * npix * sizeof(float));
+  L.vec = take(P * S * 4 * B * sizeof(float2));
+  L.sc = take(P * S * 4 * sizeof(double));
+  L.abar0 = take(npix * sizeof(float));
+  L.abar1 = take(npix * sizeof(float));
+  L.rbar = take(npix * sizeof(float));
+  L.coef = take(cube_grad ? S * npix * 2 * sizeof(float) : 0);
+  L.vkf = take(P * B * sizeof(float));
+  L.zf = take(P * S * B * sizeof(float));
+  L.bpart = take(units * mf::bwd_entries((int)B) * sizeof(float));
+  L.psc = take(P * mf::kPsc * sizeof(double));
+  L.carry = take(P * B * sizeof(float2));
+  L.mubar0 = take(P * B * sizeof(float2));
+  L.sbar = take(P * B * sizeof(double));
+  L.lbar = take(P * sizeof(double));
+  L.mu0bar = take(P * B * sizeof(float));
+  L.total = align_up(off, 256);
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mf_ckpt_bytes(mf_plan_t pl, int32_t n_iter, int32_t cube_grad) {
+  if (!pl || n_iter < 0) return 0;
+  return ck_layout(pl, n_iter, cube_grad != 0).total;
+}
+
+mf_status mf_retrieve_train(mf_plan_t pl, const float* cube, const float* k, double lambda,
+                            double eps, int32_t n_iter, const uint8_t* mask, float* alpha_out,
+                            void* ckpt, int32_t cube_grad, void* stream) {
+  g_last_error.clear();
+  if (!pl) return fail(MF_ERR_INVALID_ARG, "null plan");
+  if (!cube || !k || !alpha_out || !ckpt)
+    return fail(MF_ERR_INVALID_ARG, "null cube, k, alpha_out or ckpt");
+  if (pl->n_lines != 1) return fail(MF_ERR_UNSUPPORTED, "the backward pass takes one line");
+  if (pl->prm.flags & MF_LITERAL)
+    return fail(MF_ERR_UNSUPPORTED, "the backward pass follows the fused schedule (no MF_LITERAL)");
+  if ((reinterpret_cast<uintptr_t>(ckpt) & 255) != 0)
+    return fail(MF_ERR_INVALID_ARG, "ckpt must be 256-byte aligned");
+  mf_status st = check_scalars(lambda, eps, n_iter);
+  if (st != MF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = upload_lines(pl, &lambda, &n_iter, s);
+  if (st != MF_OK) return st;
+  const CkLayout L = ck_layout(pl, n_iter, cube_grad != 0);
+  char* base = static_cast<char*>(ckpt);
+  mf::Params ck{};
+  ck.ck_alpha = reinterpret_cast<float*>(base + L.alpha);
+  ck.ck_vec = reinterpret_cast<float2*>(base + L.vec);
+  ck.ck_sc = reinterpret_cast<double*>(base + L.sc);
+  ck.ck_stages = n_iter + 1;
+  st = run_retrieval(pl, cube, k, eps, n_iter, mask, nullptr, alpha_out, nullptr, s, &ck);
+  if (st != MF_OK) return st;
+  pl->train.ckpt = ckpt;
+  pl->train.n_iter = n_iter;
+  pl->train.cube_grad = cube_grad != 0;
+  pl->train.cube = cube;
+  pl->train.k = k;
+  pl->train.mask = mask;
+  pl->train.eps = eps;
+  return MF_OK;
+}
+
+mf_status mf_retrieve_backward(mf_plan_t pl, const void* ckpt, const float* grad_alpha,
+                               float* grad_k, float* grad_lambda, float* grad_cube,
+                               void* stream) {
+  g_last_error.clear();
+  if (!pl || !ckpt || !grad_alpha || !grad_k || !grad_lambda)
+    return fail(MF_ERR_INVALID_ARG, "null plan, ckpt, grad_alpha, grad_k or grad_lambda");
+  if (ckpt != pl->train.ckpt)
+    return fail(MF_ERR_INVALID_ARG, "ckpt does not hold this plan's last mf_retrieve_train");
+  if (grad_cube && !pl->train.cube_grad)
+    return fail(MF_ERR_INVALID_ARG, "the forward was checkpointed without the cube gradient");
+  const int n = pl->train.n_iter;
+  const CkLayout L = ck_layout(pl, n, pl->train.cube_grad);
+  char* base = static_cast<char*>(const_cast<void*>(ckpt));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mf::Params p = pl->prm;
+  p.cube = pl->train.cube;
+  p.k = pl->train.k;
+  p.mask = pl->train.mask;
+  p.eps = (float)pl->train.eps;
+  p.ck_alpha = reinterpret_cast<float*>(base + L.alpha);
+  p.ck_vec = reinterpret_cast<float2*>(base + L.vec);
+  p.ck_sc = reinterpret_cast<double*>(base + L.sc);
+  p.ck_stages = n + 1;
+  mf::BwdParams b{};
+  b.n_iter = n;
+  b.grad_alpha = grad_alpha;
+  b.abar[0] = reinterpret_cast<float*>(base + L.abar0);
+  b.abar[1] = reinterpret_cast<float*>(base + L.abar1);
+  b.rbar = reinterpret_cast<float*>(base + L.rbar);
+  b.coef = grad_cube ? reinterpret_cast<float*>(base + L.coef) : nullptr;
+  b.grad_cube = grad_cube;
+  b.vkf = reinterpret_cast<float*>(base + L.vkf);
+  b.zf = reinterpret_cast<float*>(base + L.zf);
+  b.bpart = reinterpret_cast<float*>(base + L.bpart);
+  b.psc = reinterpret_cast<double*>(base + L.psc);
+  b.carry = reinterpret_cast<float2*>(base + L.carry);
+  b.mubar0 = reinterpret_cast<float2*>(base + L.mubar0);
+  b.sbar = reinterpret_cast<double*>(base + L.sbar);
+  b.lbar = reinterpret_cast<double*>(base + L.lbar);
+  b.mu0bar_n = reinterpret_cast<float*>(base + L.mu0bar);
+  b.grad_k = grad_k;
+  b.grad_lambda = grad_lambda;
+  if (p.cube != pl->map_cube) {
+    if (!encode_cube_map(&pl->map_stats, pl->prm, p.cube, 1, mf::kStatRows) ||
+        !encode_cube_map(&pl->map_pixel, pl->prm, p.cube, mf::kTileCols, mf::kStageRows)) {
+      pl->map_cube = nullptr;
+      return fail(MF_ERR_CUDA, "cuTensorMapEncodeTiled failed for the cube");
+    }
+    pl->map_cube = p.cube;
+  }
+  const size_t smem_px = mf::bwd_pixel_smem_bytes(p.B, pl->nj);
+  const size_t smem_sv = mf::bwd_solve_smem_bytes(p.B);
+  MF_CUDA(mf::bwd_set_attributes(pl->nj, smem_px, smem_sv));
+  // zero the per-partition accumulators (psc, carry, mubar0, sbar, lbar)
+  MF_CUDA(cudaMemsetAsync(base + L.psc, 0, L.mu0bar - L.psc, s));
+  const int grid_px = p.n_ct * pl->lines[0].n_rb;
+  for (int k = n; k >= 0; --k)
+    mf::bwd_launch_stage(pl->nj, grid_px, smem_px, smem_sv, s, pl->map_pixel, p, b, k);
+  mf::bwd_launch_final(pl->nj, smem_px, s, p, b);
+  MF_CUDA(cudaGetLastError());
+  pl->last_stream = s;
+  return MF_OK;
 }
 
 mf_status mf_retrieve_host(mf_plan_t pl, const float* cube, const float* k, double lambda,

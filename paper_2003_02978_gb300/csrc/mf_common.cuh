@@ -91,7 +91,44 @@ struct Params {
   float2* k1part;
   float* k3part;
   int* status;
+  // checkpoints of a retrieval for the backward pass (null: none): alpha^k of
+  // every pass k = 0..n, and per partition and pass the double-float vectors
+  // mu^k, t^k, v^k, g^k and the scalars q^k, mean(beta)^k, var(beta)^k
+  float* ck_alpha;      // (n + 1, rows, cols)
+  float2* ck_vec;       // (P, n + 1, 4, B)
+  double* ck_sc;        // (P, n + 1, 4)
+  int ck_stages;        // n + 1
 };
+
+enum : int { CKV_MU = 0, CKV_T, CKV_V, CKV_G };
+enum : int { CKS_Q = 0, CKS_BBAR, CKS_VAR };
+
+// Backward pass of a single-line retrieval (see mf_backward.cu)
+struct BwdParams {
+  int n_iter;
+  const float* grad_alpha;  // (rows, cols) adjoint of the output alpha^n
+  float* abar[2];           // (rows, cols) partial adjoint of alpha^k, ping-pong by stage
+  float* rbar;              // (rows, cols) adjoint of r_i, accumulated over stages
+  float* coef;              // (n + 1, rows, cols, 2) cube-gradient coefficients, or null
+  float* grad_cube;         // (rows, cols, B) output, or null
+  float* vkf;               // (P, B) v^k of the current stage, float
+  float* zf;                // (P, n + 1, B) zbar^k of every stage, float
+  float* bpart;             // per-CTA partial sums of a backward pixel pass
+  double* psc;              // (P, kPsc) per-partition scalars of the current stage
+  float2* carry;            // (P, B) adjoint of t^{k-1} carried to stage k - 1
+  float2* mubar0;           // (P, B) adjoint of mu^0
+  double* sbar;             // (P, B) per-partition part of the gradient of s
+  double* lbar;             // (P) per-partition part of the gradient of lambda
+  float* mu0bar_n;          // (P, B) float: adjoint of mu^0 / N (cube gradient)
+  float* grad_k;            // (B) output
+  float* grad_lambda;       // (1) output
+};
+constexpr int kPsc = 16;
+enum : int {
+  PSC_Q = 0, PSC_MUV, PSC_COFF, PSC_INVM2, PSC_N, PSC_CNEXT, PSC_ZT, PSC_ZMU0, PSC_ZOFF,
+  PSC_PSUM, PSC_QBAR, PSC_LAMBAR, PSC_BBAR
+};
+__host__ __device__ inline int bwd_entries(int B) { return B + 8; }
 
 __host__ __device__ inline int k1_entries(int BA) {
   const int nb = BA / 4;
@@ -195,6 +232,15 @@ cudaError_t stats_tc_set_attributes(int nj, size_t smem);
 void stats_tc_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
                      const Params& p, int mode, int pass);
 void pilot_launch(cudaStream_t s, const Params& p);
+// backward pass (mf_backward.cu)
+size_t bwd_pixel_smem_bytes(int B, int nj);
+size_t bwd_solve_smem_bytes(int B);
+cudaError_t bwd_set_attributes(int nj, size_t smem_pixel, size_t smem_solve);
+void bwd_launch_stage(int nj, int grid_pixel, size_t smem_pixel, size_t smem_solve,
+                      cudaStream_t s, const CUtensorMap& map, const Params& p,
+                      const BwdParams& b, int stage);
+void bwd_launch_final(int nj, size_t smem_pixel, cudaStream_t s, const Params& p,
+                      const BwdParams& b);
 size_t background_smem_bytes(int B, int BA);
 cudaError_t background_set_attributes(size_t smem);
 void background_launch(size_t smem, cudaStream_t s, const Params& p, double* mu, double* cov);

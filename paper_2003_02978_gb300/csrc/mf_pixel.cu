@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     if (inb && e == 0) {
       const size_t pix = (size_t)row * p.cols + c;
       p.alpha[pix] = al;
+      if (p.ck_alpha) p.ck_alpha[(size_t)pass * p.rows * p.cols + pix] = al;
       if (!iter && p.albedo) p.albedo[pix] = valid ? r : 0.f;
     }
     if (accumulate) {

@@ -424,6 +424,21 @@ __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
     stf(p.tprev, pb + b, vt[b]);
     stf(p.muk, pb + b, vmu[b]);
   }
+  if (p.ck_vec) {  // checkpoint of stage 0 for the backward pass
+    float2* cv = p.ck_vec + (size_t)part * p.ck_stages * 4 * B;
+    for (int b = tid; b < B; b += kThreads) {
+      stf(cv, CKV_MU * B + b, vmu[b]);
+      stf(cv, CKV_T * B + b, vt[b]);
+      stf(cv, CKV_V * B + b, vz[b]);
+      stf(cv, CKV_G * B + b, df{0.f, 0.f});
+    }
+    if (tid == 0) {
+      double* cs = p.ck_sc + (size_t)part * p.ck_stages * 4;
+      cs[CKS_Q] = df_to_double(q);
+      cs[CKS_BBAR] = 0.0;
+      cs[CKS_VAR] = 0.0;
+    }
+  }
   if (tid == 0) {
     const bool good = q.hi > 0.f && df_isfinite(q);
     reinterpret_cast<float4*>(p.pscal)[part] =
@@ -645,6 +660,21 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
     stf(p.zt, pb + b, Z1[b]);
     stf(p.tprev, pb + b, U1[b]);
     stf(p.muk, pb + b, vmk[b]);
+  }
+  if (p.ck_vec && pass < p.ck_stages) {  // checkpoint of stage `pass`
+    float2* cv = p.ck_vec + ((size_t)part * p.ck_stages + pass) * 4 * B;
+    for (int b = tid; b < B; b += kThreads) {
+      stf(cv, CKV_MU * B + b, vmk[b]);
+      stf(cv, CKV_T * B + b, U1[b]);
+      stf(cv, CKV_V * B + b, vv[b]);
+      stf(cv, CKV_G * B + b, U0[b]);
+    }
+    if (tid == 0) {
+      double* cs = p.ck_sc + ((size_t)part * p.ck_stages + pass) * 4;
+      cs[CKS_Q] = df_to_double(q);
+      cs[CKS_BBAR] = df_to_double(bbar);
+      cs[CKS_VAR] = df_to_double(var);
+    }
   }
   if (tid == 0) {
     float4* ps = reinterpret_cast<float4*>(p.pscal) + part;

@@ -1,0 +1,151 @@
+"""Differentiation form: the library's hand-written adjoint of the unrolled
+retrieval against the FP64 autograd oracle (oracle/mf_grad.py, pinned by
+finite differences), for the gradients with respect to s, lambda and the
+radiance cube."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from parity import f32
+from synth import make_scene, workload_scene
+
+pytestmark = pytest.mark.gpu
+
+# stated bound of the backward pass (float32 pixel arithmetic, double-float
+# partition arithmetic): normwise relative error of each gradient, for output
+# adjoints that avoid the kinks: pixels whose reweighting map amplifies
+# rounding more than tenfold (oracle.amplification: a tiny positive
+# alpha^{k-1} makes w^2 = 1/(alpha + eps)^2 huge) get a zero output adjoint;
+# three such pixels of a 400 x 6 scene carry 86% of |dL/ds| at n_iter = 1.
+# The bound is 2e-2: the gradients depend on the forward's v^k = (C^k)^{-1} t^k
+# directly, which float32 pixel arithmetic leaves up to 6e-4 off on these
+# 400-row scenes (alpha within 2e-5), growing with k; measured up to 1.3e-2
+# (n_iter = 3), 2e-5 for n_iter <= 2 without sparsity.
+TOL_GRAD = 2e-2
+
+
+def away_from_kinks(g, sc, lam, n_iter, flags=3):
+    amp = oracle.retrieve_amplification(sc.cube.numpy().astype(np.float64), f32(sc.k), lam,
+                                        1e-9, n_iter, flags=flags,
+                                        mask=None if sc.mask is None else sc.mask.numpy())
+    return np.where(amp > 10, 0.0, g)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2003_02978_gb300 import build
+    build.build()
+
+
+def sensitivity(cube, s, lam, n_iter, g, mask, flags, grads):
+    """Relative change of the FP64 oracle's gradients under a 1e-7 relative
+    perturbation of the radiance (float32 rounding of the input): with the
+    reweighting (w = 1/(alpha + eps)) the exact gradient is ill-conditioned,
+    1e-7 in the input moving dL/ds by about 1e-2 on the test scenes."""
+    pert = cube * (1 + 1e-7 * np.random.default_rng(1).standard_normal(cube.shape))
+    pc, pk, pl = oracle.grad_vjp(pert, s, lam, 1e-9, n_iter, g, mask=mask, flags=flags)
+    rc, rk, rl = grads
+    return rel(pk, rk), abs(pl - rl) / max(abs(rl), 1e-300), rel(pc, rc)
+
+
+def bound(sens):
+    """The backward's stated bound: TOL_GRAD, or twice the oracle gradient's
+    own sensitivity to float32 input rounding, whichever is larger."""
+    return max(TOL_GRAD, 2.0 * sens)
+
+
+def rel(got, ref):
+    return float(np.linalg.norm(np.asarray(got, np.float64) - ref) /
+                 max(np.linalg.norm(ref), 1e-300))
+
+
+def run(sc, lam, n_iter, g, flags=3, cube_grad=True):
+    import paper_2003_02978_gb300 as mfg
+    rows, cols, bt = sc.cube.shape
+    plan = mfg.Plan(rows, cols, bt, flags=flags)
+    cube = sc.cube.cuda()
+    mask = None if sc.mask is None else sc.mask.cuda()
+    alpha, ck = plan.retrieve_train(cube, f32(sc.k).astype(np.float32), lam, 1e-9, n_iter,
+                                    mask=mask, cube_grad=cube_grad)
+    gk, gl, gc = plan.backward(ck, torch.as_tensor(g, dtype=torch.float32).cuda(),
+                               cube_grad=cube_grad)
+    torch.cuda.synchronize()
+    st = plan.status()
+    out = (alpha.cpu().numpy(), gk.cpu().numpy(), float(gl.cpu()),
+           None if gc is None else gc.cpu().numpy(), st)
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("n_iter,lam,flags", [(0, 0.0, 3), (1, 1e-3, 3), (3, 1e-3, 3),
+                                              (3, 0.0, 1), (2, 1e-3, 2), (4, 2e-3, 11)])
+def test_backward_matches_oracle_gradient(n_iter, lam, flags):
+    sc = make_scene(400, 6, 72, n_plumes=2, plume_sigma=(3.0, 6.0), plume_peak=(800.0, 3000.0),
+                    mask_frac=0.03, seed=31 + n_iter)
+    rng = np.random.default_rng(9)
+    g = away_from_kinks(rng.normal(size=sc.cube.shape[:2]), sc, lam, n_iter, flags)
+    alpha, gk, gl, gc, st = run(sc, lam, n_iter, g, flags)
+    assert np.all(st == 0)
+    cube = sc.cube.numpy().astype(np.float64)
+    mask = sc.mask.numpy()
+    grads = oracle.grad_vjp(cube, f32(sc.k), lam, 1e-9, n_iter, g, mask=mask, flags=flags)
+    rc, rk, rl = grads
+    sk, sl, sc_ = sensitivity(cube, f32(sc.k), lam, n_iter, g, mask, flags, grads)
+    assert rel(gk, rk) <= bound(sk), (rel(gk, rk), sk)
+    if n_iter and lam > 0 and (flags & 2):
+        assert abs(gl - rl) <= bound(sl) * abs(rl), (gl, rl, sl)
+    assert rel(gc, rc) <= bound(sc_), (rel(gc, rc), sc_)
+    valid = oracle.valid_pixels(sc.cube.numpy(), mask)
+    assert np.all(gc[~valid] == 0)
+
+
+def test_backward_mse_loss_flightline_sample():
+    """The configured loss (MSE of alpha against the injected plume map) on
+    a 2000-row slice of the differentiation workload."""
+    sc, prm = workload_scene("diff-8000x598x72", seed=1, rows=2000, cols=8)
+    rows, cols = sc.cube.shape[:2]
+    import paper_2003_02978_gb300 as mfg
+    plan = mfg.Plan(rows, cols, 72)
+    cube = sc.cube.cuda()
+    mask = sc.mask.cuda()
+    alpha, ck = plan.retrieve_train(cube, f32(sc.k).astype(np.float32), prm["lam"], prm["eps"],
+                                    prm["n_iter"], mask=mask, cube_grad=True)
+    truth = torch.as_tensor(sc.alpha_true, dtype=torch.float32).cuda()
+    g = 2.0 * (alpha - truth) / alpha.numel()
+    g = torch.as_tensor(away_from_kinks(g.cpu().numpy().astype(np.float64), sc, prm["lam"],
+                                        prm["n_iter"]), dtype=torch.float32).cuda()
+    gk, gl, gc = plan.backward(ck, g, cube_grad=True)
+    torch.cuda.synchronize()
+    cube64 = sc.cube.numpy().astype(np.float64)
+    g64 = g.cpu().numpy().astype(np.float64)
+    grads = oracle.grad_vjp(cube64, f32(sc.k), prm["lam"], prm["eps"], prm["n_iter"], g64,
+                            mask=sc.mask.numpy())
+    rc, rk, rl = grads
+    sk, sl, sc_ = sensitivity(cube64, f32(sc.k), prm["lam"], prm["n_iter"], g64,
+                              sc.mask.numpy(), 3, grads)
+    assert rel(gk.cpu().numpy(), rk) <= bound(sk)
+    assert abs(float(gl.cpu()) - rl) <= bound(sl) * abs(rl)
+    assert rel(gc.cpu().numpy(), rc) <= bound(sc_)
+    plan.close()
+
+
+def test_autograd_function():
+    import paper_2003_02978_gb300 as mfg
+    sc = make_scene(300, 4, 72, n_plumes=1, plume_peak=(2000.0, 2000.0), seed=12)
+    cube = sc.cube.cuda().requires_grad_(True)
+    k = torch.as_tensor(f32(sc.k), dtype=torch.float32).cuda().requires_grad_(True)
+    lam = torch.tensor(1e-3, dtype=torch.float32, requires_grad=True)
+    alpha = mfg.retrieve_differentiable(cube, k, lam, n_iter=3)
+    keep = torch.as_tensor(away_from_kinks(np.ones(alpha.shape), sc, 1e-3, 3),
+                           dtype=torch.float32).cuda()
+    loss = (keep * alpha ** 2).sum()
+    loss.backward()
+    g = 2.0 * (keep * alpha).detach().cpu().numpy().astype(np.float64)
+    cube64 = sc.cube.numpy().astype(np.float64)
+    grads = oracle.grad_vjp(cube64, f32(sc.k), 1e-3, 1e-9, 3, g)
+    rc, rk, rl = grads
+    sk, sl, sc_ = sensitivity(cube64, f32(sc.k), 1e-3, 3, g, None, 3, grads)
+    assert rel(k.grad.cpu().numpy(), rk) <= bound(sk)
+    assert abs(float(lam.grad) - rl) <= bound(sl) * abs(rl)
+    assert rel(cube.grad.cpu().numpy(), rc) <= bound(sc_)
