@@ -305,6 +305,57 @@ def batched_form(args, dev, precision):
             "status_ok": status_ok, "alpha_error": err}
 
 
+def differentiation_form(args, dev):
+    """Forward with checkpoints and the backward pass (gradients for s, lambda
+    and the cube) on the differentiation workload (8000 x 598 x 72, 10
+    iterations, loss = MSE of alpha against the injected plume map), timed
+    with CUDA events; the target is backward <= 3 x forward."""
+    import torch
+    import paper_2003_02978_gb300 as mfg
+    from synth import workload_scene
+    sc, prm = workload_scene("diff-8000x598x72", seed=3, device=dev)
+    rows, cols, bands = sc.cube.shape
+    k = torch.as_tensor(np.asarray(sc.k, np.float32), device=dev)
+    plan = mfg.Plan(rows, cols, bands)
+    ck = torch.empty(plan.ckpt_bytes(prm["n_iter"], True) + 256, dtype=torch.uint8, device=dev)
+    truth = torch.as_tensor(sc.alpha_true, dtype=torch.float32, device=dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    fw, bw_ = [], []
+    for it in range(4):
+        e[0].record()
+        alpha, _ = plan.retrieve_train(sc.cube, k, prm["lam"], prm["eps"], prm["n_iter"],
+                                       mask=sc.mask, cube_grad=True, ckpt=ck)
+        e[1].record()
+        g = 2.0 * (alpha - truth) / alpha.numel()
+        e[2].record()
+        plan.backward(ck, g, cube_grad=True)
+        e[3].record()
+        torch.cuda.synchronize()
+        if it >= 1:
+            fw.append(e[0].elapsed_time(e[1]))
+            bw_.append(e[2].elapsed_time(e[3]))
+    # forward of the same plan without checkpoints (graph replay), for the ratio
+    out = torch.empty((rows, cols), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        plan.retrieve(sc.cube, k, prm["lam"], prm["eps"], prm["n_iter"], mask=sc.mask, out=out)
+    torch.cuda.synchronize()
+    e[0].record()
+    for _ in range(5):
+        plan.retrieve(sc.cube, k, prm["lam"], prm["eps"], prm["n_iter"], mask=sc.mask, out=out)
+    e[1].record()
+    torch.cuda.synchronize()
+    f_plain = e[0].elapsed_time(e[1]) / 5
+    st_ok = bool(np.all(plan.status() == 0))
+    plan.close()
+    del ck, sc
+    torch.cuda.empty_cache()
+    f_ms, b_ms = float(np.median(fw)), float(np.median(bw_))
+    return {"workload": f"diff-{rows}x{cols}x{bands}, n_iter {prm['n_iter']}, MSE loss, "
+                        "gradients for s, lambda and the cube",
+            "forward_ckpt_ms": f_ms, "forward_ms": f_plain, "backward_ms": b_ms,
+            "backward_over_forward": b_ms / f_plain, "status_ok": st_ok}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,6 +364,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle checks")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation-form timing")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -437,6 +489,9 @@ def main():
     batched = None
     if not args.no_batched and rank == 0:
         batched = batched_form(args, dev, mfg.BF16SPLIT)
+    differentiation = None
+    if not args.no_diff and rank == 0:
+        differentiation = differentiation_form(args, dev)
 
     result = {}
     if rank == 0:
@@ -502,6 +557,7 @@ def main():
                     "api": "mf_retrieve_host (pinned host buffers)"},
             "cpu_baseline": cpu,
             "batched": batched,
+            "differentiation": differentiation,
             "clocks": clocks,
         }
         print(json.dumps(result), flush=True)
