@@ -37,6 +37,7 @@
 // is double-float.
 #include "mf_common.cuh"
 #include "mf_df.cuh"
+#include "mf_dense.cuh"
 #include "mf_pixel_io.cuh"
 #include "mf_tma.cuh"
 #include "../../include/mf.h"
@@ -100,7 +101,7 @@ __device__ df block_dot(const df* a, const df* b, int n, df* red) {
 }  // namespace
 
 size_t bwd_pixel_smem_bytes(int B, int nj) { return bw_layout(B, 8 * nj).total + 128; }
-size_t bwd_solve_smem_bytes(int B) { return ((size_t)B * B + 12 * (size_t)B) * sizeof(df) + 64; }
+size_t bwd_solve_smem_bytes(int B) { return ((size_t)B * linv_ld(B) + 20 * (size_t)B) * sizeof(df) + 64; }
 
 // ---------------------------------------------------------------- pre(k)
 // per-partition float scalars and v^k of stage k for the pixel passes
@@ -400,31 +401,16 @@ __global__ void __launch_bounds__(kBwThreads, 1)
 namespace {
 // Y = L^{-1} U, Z = L^{-T} Y for nr right-hand sides (columns of U, B each),
 // L^{-1} row-major lower (diagonal included) in X; compensated dots
-__device__ void c0inv(const df* X, int B, const df* const* U, df* const* Y, df* const* Z, int nr) {
-  for (int w = threadIdx.x; w < nr * B; w += kThreads) {
-    const int r = w / B, i = w % B;
-    df s{0.f, 0.f};
-    for (int j = 0; j <= i; ++j) s = df_fma(X[i * B + j], U[r][j], s);
-    Y[r][i] = s;
-  }
-  __syncthreads();
-  for (int w = threadIdx.x; w < nr * B; w += kThreads) {
-    const int r = w / B, j = w % B;
-    df s{0.f, 0.f};
-    for (int i = j; i < B; ++i) s = df_fma(X[i * B + j], Y[r][i], s);
-    Z[r][j] = s;
-  }
-  __syncthreads();
-}
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) bwd_solve_kernel(Params p, BwdParams b, int k) {
+__global__ void __launch_bounds__(kThreads, 4) bwd_solve_kernel(Params p, BwdParams b, int k) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ df red[kWarps];
   __shared__ df s_sc[8];
   __shared__ df s_W[16];
   __shared__ df s_c[3];
   __shared__ int s_bad;
+  __shared__ __align__(8) uint64_t s_xbar;
   const int part = blockIdx.x, tid = threadIdx.x, B = p.B;
   const int S = p.ck_stages;
   const size_t pb = (size_t)part * B;
@@ -434,8 +420,12 @@ __global__ void __launch_bounds__(kThreads) bwd_solve_kernel(Params p, BwdParams
     if (tid == 0) ps[PSC_ZT] = ps[PSC_ZMU0] = ps[PSC_ZOFF] = ps[PSC_PSUM] = ps[PSC_QBAR] = 0.0;
     return;
   }
-  df* X = reinterpret_cast<df*>(smem_raw);  // L^{-1}
-  df* vb = X + (size_t)B * B;                // vbar
+  df* X = reinterpret_cast<df*>(smem_raw);  // L^{-1} (ld linv_ld(B)), later the direct path's matrix
+  float4* UP0 = reinterpret_cast<float4*>(X + (size_t)B * linv_ld(B));  // (vbar, g) interleaved
+  float4* UP1 = UP0 + B;                                               // (t^k, d) interleaved
+  float4* YP0 = UP1 + B;
+  float4* YP1 = YP0 + B;
+  df* vb = reinterpret_cast<df*>(YP1 + B);   // vbar
   df* G = vb + B;
   df* T = G + B;                             // t^k
   df* D = T + B;                             // t^{k-1} - t^k
@@ -448,6 +438,16 @@ __global__ void __launch_bounds__(kThreads) bwd_solve_kernel(Params p, BwdParams
   df* Z2 = Z1 + B;
   df* Z3 = Z2 + B;
   const int E = bwd_entries(B);
+  // L^{-1} of the partition into shared memory by one bulk copy, in flight
+  // during the reductions below
+  if (tid == 0) {
+    const size_t n = (size_t)B * linv_ld(B);
+    const uint32_t bytes = (uint32_t)(n * sizeof(float2));
+    mbar_init(&s_xbar, 1);
+    mbar_fence_init();
+    mbar_arrive_expect_tx(&s_xbar, bytes);
+    bulk_load(X, p.Linv + (size_t)part * n, bytes, &s_xbar);
+  }
   if (tid < 4) s_sc[tid] = reduce_units(p, part, b.bpart, E, tid);
   const float2* cv = p.ck_vec + ((size_t)part * S + k) * 4 * B;
   __syncthreads();
@@ -463,21 +463,28 @@ __global__ void __launch_bounds__(kThreads) bwd_solve_kernel(Params p, BwdParams
     T[j] = tk;
     G[j] = ldf(cv, CKV_G * B + j);
     D[j] = k > 0 ? df_sub(ldf(cv - 4 * B, CKV_T * B + j), tk) : df{0.f, 0.f};
+    UP0[j] = pack_pair(vb[j], G[j]);
+    UP1[j] = pack_pair(T[j], D[j]);
   }
-  const float2* Xg = p.Linv + (size_t)part * B * B;
-  for (int idx = tid; idx < B * B; idx += kThreads) X[idx] = ldf(Xg, idx);
   __syncthreads();
+  if (!__syncthreads_and(mbar_wait(&s_xbar, 0))) {
+    // the copy did not complete in time (uniform decision): record it, give
+    // the copy a second bounded wait and leave
+    if (tid == 0) p.status[part] = MF_ERR_TIMEOUT;
+    mbar_wait(&s_xbar, 0);
+    return;
+  }
   df* zb = Z0;
   if (k == 0) {
-    const df* U[1] = {vb};
-    df* Yv[1] = {Y0};
-    df* Zv[1] = {Z0};
-    c0inv(X, B, U, Yv, Zv, 1);
+    const float4* U[1] = {UP0};  // (vbar, g = 0)
+    float4* Yv[1] = {YP0};
+    df* Zv[2] = {Z0, Z1};
+    c0inv_apply<1>(X, B, U, Yv, Zv);
   } else {
-    const df* U[4] = {vb, G, T, D};
-    df* Yv[4] = {Y0, Y1, Y2, Y3};
+    const float4* U[2] = {UP0, UP1};
+    float4* Yv[2] = {YP0, YP1};
     df* Zv[4] = {Z0, Z1, Z2, Z3};
-    c0inv(X, B, U, Yv, Zv, 4);
+    c0inv_apply<2>(X, B, U, Yv, Zv);
     // W = U^T C0^{-1} U (3 x 3, U = [g, t, d]) and U^T C0^{-1} vbar
     const df* ua[12] = {G, G, G, T, T, T, D, D, D, G, T, D};
     const df* zv[12] = {Z1, Z2, Z3, Z1, Z2, Z3, Z1, Z2, Z3, Z0, Z0, Z0};
@@ -546,48 +553,8 @@ __global__ void __launch_bounds__(kThreads) bwd_solve_kernel(Params p, BwdParams
         c = df_fma(mb2, df_mul(D[i], D[j]), c);
         Xm.set(i, j, c);
       }
-      for (int j = tid; j < B; j += kThreads) Z0[j] = vb[j];
-      __syncthreads();
-      bool ok = true;
-      {
-        // upper Cholesky and two substitutions (Y1 holds 1/diag(U))
-        const int lane = tid & 31, warp = tid >> 5;
-        for (int j = 0; j < B && ok; ++j) {
-          const df d = Xm.get(j, j);
-          if (!(d.hi > 0.f) || !df_isfinite(d)) {
-            ok = false;
-            break;
-          }
-          const df r = df_rsqrt(d), rinv = df_mul(r, r);
-          if (j > 0)
-            for (int kk = j + tid; kk < B; kk += kThreads)
-              Xm.set(j - 1, kk, df_mul(Xm.get(j - 1, kk), Y1[j - 1]));
-          for (int i = j + 1 + warp; i < B; i += kWarps) {
-            const df w = df_mul(Xm.get(j, i), rinv);
-            for (int kk = i + lane; kk < B; kk += 32)
-              Xm.set(i, kk, df_sub(Xm.get(i, kk), df_mul(w, Xm.get(j, kk))));
-          }
-          if (tid == 0) Y1[j] = r;
-          __syncthreads();
-        }
-        if (ok) {
-          // U^T y = vbar, then U z = y (U's rows scaled, 1/U_jj in Y1)
-          for (int j = 0; j < B; ++j) {
-            __syncthreads();
-            if (tid == 0) Z0[j] = df_mul(Z0[j], Y1[j]);
-            __syncthreads();
-            for (int i = j + 1 + tid; i < B; i += kThreads)
-              Z0[i] = df_sub(Z0[i], df_mul(Xm.get(j, i), Z0[j]));
-          }
-          for (int j = B - 1; j >= 0; --j) {
-            __syncthreads();
-            if (tid == 0) Z0[j] = df_mul(Z0[j], Y1[j]);
-            __syncthreads();
-            for (int i = tid; i < j; i += kThreads) Z0[i] = df_sub(Z0[i], df_mul(Xm.get(i, j), Z0[j]));
-          }
-          __syncthreads();
-        }
-      }
+      const bool ok = chol_inv_df(Xm, B, Y1);  // Y1 holds 1/diag(U)
+      if (ok) xtx_apply_df(Xm, B, Y1, vb, Y2, Z0);
       if (!ok) {
         if (tid == 0) p.status[part] = MF_ERR_NOT_SPD;
         for (int j = tid; j < B; j += kThreads) Z0[j] = df{0.f, 0.f};

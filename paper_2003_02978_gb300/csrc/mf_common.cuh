@@ -14,7 +14,8 @@
 //   tprev      (P, B) double-float   target t(mu^k) of the last statistics
 //   muk        (P, B) double-float   mean mu^k (literal schedule)
 //   S          (P, B, B) float64     C^0 (read back by mf_background)
-//   Linv       (P, B, B) double-float inverse of the Cholesky factor of C^0 (lower)
+//   Linv       (P, B, B + 1) double-float inverse of the Cholesky factor of C^0 (lower,
+//              rows padded by one entry)
 //   pscal      (P, 4) float32        q, mu0f.v, (mu^k - mu0f).v, 1/(mu0f.mu0f)
 //   dscal      (P, 4) float64        N, mean(beta), q
 //   k1part     (P, G * n_sc, K1E) double-float   per-CTA augmented second moments

@@ -102,7 +102,8 @@ __device__ __forceinline__ bool df_isfinite(df x) { return isfinite(x.hi) && isf
 
 // A double-float matrix in shared memory stored as two float planes (hi at
 // h[i * ld + j], lo one plane further), so that adjacent elements of a row
-// load as float2 pairs for the packed arithmetic below.  ld is even.
+// load as float2 pairs for the packed arithmetic below.  ld is even (a
+// multiple of 4, with a 16-byte aligned base, for the float4 loads).
 struct DfMat {
   float* h;
   int ld;
@@ -124,6 +125,13 @@ struct DfMat {
   __device__ __forceinline__ void set2(int i, int j, float2 hi, float2 lo) const {
     *reinterpret_cast<float2*>(h + i * ld + j) = hi;
     *reinterpret_cast<float2*>(h + plane + i * ld + j) = lo;
+  }
+  // elements (i, j .. j + 3), j and ld multiples of 4, plane a multiple of 4
+  __device__ __forceinline__ float4 hi4(int i, int j) const {
+    return *reinterpret_cast<const float4*>(h + i * ld + j);
+  }
+  __device__ __forceinline__ float4 lo4(int i, int j) const {
+    return *reinterpret_cast<const float4*>(h + plane + i * ld + j);
   }
 };
 

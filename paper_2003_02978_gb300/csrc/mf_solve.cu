@@ -4,8 +4,9 @@
 // solve_init (after the initial statistics pass; Fig. 1 initialisation):
 //   reduce the per-CTA augmented moments, assemble mu^0 and
 //   C^0 = (1/N) sum (x_i - mu^0)(x_i - mu^0)^T exactly from them, factorise
-//   C^0 = L L^T (Cholesky), form L^{-1} in place, and solve C^0 v = t^0 with
-//   t^0 = mu^0 (.) s (Eq. (9)); q = t^T v is the normaliser of Eq. (3).
+//   C^0 = L L^T (blocked Cholesky, L^{-1} formed in the same sweep), and
+//   solve C^0 v = t^0 with t^0 = mu^0 (.) s (Eq. (9)); q = t^T v is the
+//   normaliser of Eq. (3).
 // solve_iter (after each pixel pass; Fig. 1 loop body, Eqs. (10)-(11)):
 //   mu^{k+1} = mu^0 - mean(beta) t^k and, with t = t^{k+1},
 //   d = t^k - t^{k+1} and g = mean(beta (x - mu^0)),
@@ -20,6 +21,8 @@
 //   fresh statistics pass over d_i, factorise and solve, every iteration.
 #include "mf_common.cuh"
 #include "mf_df.cuh"
+#include "mf_dense.cuh"
+#include "mf_tma.cuh"
 #include "../../include/mf.h"
 
 namespace mf {
@@ -32,10 +35,6 @@ __device__ __forceinline__ df ldf(const float2* p, size_t i) {
 }
 __device__ __forceinline__ void stf(float2* p, size_t i, df v) { p[i] = make_float2(v.hi, v.lo); }
 
-__device__ __forceinline__ df shfl_xor_df(df v, int o) {
-  return df{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-}
-
 __device__ __forceinline__ df shfl_df(df v, int src) {
   return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
 }
@@ -43,7 +42,7 @@ __device__ __forceinline__ df shfl_df(df v, int src) {
 // CTA-wide double-float sum, fixed order; every thread gets the result
 __device__ df block_sum_df(df v, df* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_xor_df(v, o));
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) red[w] = v;
@@ -53,20 +52,6 @@ __device__ df block_sum_df(df v, df* red) {
   return s;
 }
 
-// compensated accumulation of products (Dot2 of Ogita, Rump and Oishi, with
-// double-float factors; the lo*lo product is dropped)
-struct Dot2 {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(df x, df y) {
-    const df pr = two_prod(x.hi, y.hi);
-    const float err = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, pr.lo));
-    const df t = two_sum(s, pr.hi);
-    s = t.hi;
-    c = __fadd_rn(c, __fadd_rn(t.lo, err));
-  }
-  __device__ __forceinline__ df result() const { return fast_two_sum(s, c); }
-};
-
 // dot product of length n by one warp (lanes stride the index), all lanes
 // get the result
 __device__ __forceinline__ df warp_dot_df(const df* a, const df* b, int n) {
@@ -74,7 +59,7 @@ __device__ __forceinline__ df warp_dot_df(const df* a, const df* b, int n) {
   for (int i = threadIdx.x & 31; i < n; i += 32) d.add(a[i], b[i]);
   df v = d.result();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_xor_df(v, o));
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
   return v;
 }
 
@@ -93,20 +78,6 @@ __device__ df block_dot_df(const df* a, const df* b, int n, df* red) {
   Dot2 d;
   for (int i = threadIdx.x; i < n; i += kThreads) d.add(a[i], b[i]);
   return block_sum_df(d.result(), red);
-}
-
-// block t of the packed upper-triangular list of nb x nb blocks -> (bi, bj):
-// row r starts at r nb - r (r - 1) / 2 (closed form, corrected by one)
-__device__ __forceinline__ void block_rc(int t, int nb, int& bi, int& bj) {
-  const float b2 = 2.f * nb + 1.f;
-  int r = (int)((b2 - sqrtf(b2 * b2 - 8.f * (float)t)) * 0.5f);
-  auto start = [&](int x) { return x * nb - (x * (x - 1)) / 2; };
-  if (r < 0) r = 0;
-  if (r > nb - 1) r = nb - 1;
-  if (start(r) > t) --r;
-  else if (r + 1 < nb && start(r + 1) <= t) ++r;
-  bi = r;
-  bj = r + (t - start(r));
 }
 
 // reduce the per-CTA augmented moments of `part` into the full symmetric
@@ -138,7 +109,7 @@ __device__ void reduce_k1(const Params& p, int part, const DfMat& A) {
       const int q = q0 + h * kThreads;
       if (q >= K1E) continue;
       int bi, bj;
-      block_rc(q >> 4, nb, bi, bj);
+      tri_decode(q >> 4, nb, bi, bj);
       const int w = q & 15;
       const int i = 4 * bi + (w >> 2), j = 4 * bj + (w & 3);
       A.set(i, j, sum[h]);
@@ -209,109 +180,6 @@ __device__ void assemble(const Params& p, const DfMat& A, const df* u1, const df
   __syncthreads();
 }
 
-// In-place Cholesky C = U^T U of the upper triangle (diagonal included) of
-// the leading n x n block (n even); the strict lower triangle is not
-// referenced (it may be overwritten).  Right-looking, one row per step and
-// one barrier per step: step j reads the pivot d = A_jj (final since step
-// j-1) and the unscaled row j, updates rows i > j as
-// A_ik -= (A_ji / d) A_jk (k >= i; warps take rows, lanes the contiguous k
-// in packed pairs), and scales row j-1 by its 1/U (row j-1 is no longer
-// read).  invd[j] = 1/U_jj; U's diagonal is written after the loop.
-// Returns false (uniformly: every thread reads the same pivot) if a pivot
-// is not > 0.
-__device__ bool cholesky_upper_df(const DfMat& A, int n, df* invd) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    const df d = A.get(j, j);
-    if (!(d.hi > 0.f) || !df_isfinite(d)) return false;
-    const df r = df_rsqrt(d);      // 1/sqrt(d), same in every thread
-    const df rinv = df_mul(r, r);  // 1/d
-    if (j > 0) {
-      const df rp = invd[j - 1];
-      for (int k = j + tid; k < n; k += kThreads) A.set(j - 1, k, df_mul(A.get(j - 1, k), rp));
-    }
-    for (int i = j + 1 + warp; i < n; i += kWarps) {
-      const df w = df_mul(A.get(j, i), rinv);
-      // pairs (k, k + 1) from the even k <= i; k = i - 1 lies in the
-      // unreferenced lower triangle
-      for (int k = (i & ~1) + 2 * lane; k < n; k += 64) {
-        float2 ch = A.hi2(i, k), cl = A.lo2(i, k);
-        df2_fnma(ch, cl, w.hi, -w.hi, w.lo, A.hi2(j, k), A.lo2(j, k));
-        A.set2(i, k, ch, cl);
-      }
-    }
-    if (tid == 0) invd[j] = r;
-    __syncthreads();
-  }
-  for (int j = tid; j < n; j += kThreads) A.set(j, j, df_recip(invd[j]));
-  __syncthreads();
-  return true;
-}
-
-// X = L^{-1}, L = U^T (U from cholesky_upper_df, upper triangle of A), into
-// the strict lower triangle of A (A[r][j] = X[r][j], j < r); X's diagonal
-// is invd.  Right-looking elimination of L X = I with unscaled rows R
-// (X[i][.] = R[i][.] / L_ii): step i updates the rows r > i as
-// R[r][j] -= (L_ri / L_ii) R[i][j], j <= i (R[i][i] = 1; warps take rows,
-// lanes the contiguous j in packed pairs), one barrier per step; the rows
-// are scaled after the loop.
-__device__ void tri_inverse_df(const DfMat& A, int n, const df* invd) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int idx = tid; idx < n * n; idx += kThreads) {
-    const int r = idx / n, j = idx % n;
-    if (j < r) A.set(r, j, df{0.f, 0.f});
-  }
-  __syncthreads();
-  for (int i = 0; i + 1 < n; ++i) {
-    const df di = invd[i];
-    for (int r = i + 1 + warp; r < n; r += kWarps) {
-      const df w = df_mul(A.get(i, r), di);  // U[i][r] = L[r][i]
-      for (int j = 2 * lane; j <= i; j += 64) {
-        float2 ah = A.hi2(i, j), al = A.lo2(i, j);
-        // R[i][i] = 1; column i + 1 of row r is not part of this step
-        if (j == i) ah.x = 1.f, al.x = 0.f;
-        if (j + 1 == i) ah.y = 1.f, al.y = 0.f;
-        float2 ch = A.hi2(r, j), cl = A.lo2(r, j);
-        const float2 oh = ch, ol = cl;
-        df2_fnma(ch, cl, w.hi, -w.hi, w.lo, ah, al);
-        if (j + 1 > i) ch.y = oh.y, cl.y = ol.y;
-        A.set2(r, j, ch, cl);
-      }
-    }
-    __syncthreads();
-  }
-  for (int r = 1 + warp; r < n; r += kWarps) {
-    const df dr = invd[r];
-    for (int j = 2 * lane; j < r; j += 64) {
-      float2 ch = A.hi2(r, j), cl = A.lo2(r, j);
-      const float2 oh = ch, ol = cl;
-      df2_mul1(ch, cl, dr);
-      if (j + 1 >= r) ch.y = oh.y, cl.y = ol.y;  // the diagonal is not stored here
-      A.set2(r, j, ch, cl);
-    }
-  }
-  __syncthreads();
-}
-
-// solve (U^T U) x = b in place (single right-hand side), U upper in A
-__device__ void chol_solve_df(const DfMat& A, int n, const df* invd, df* x) {
-  const int tid = threadIdx.x;
-  for (int j = 0; j < n; ++j) {
-    __syncthreads();
-    if (tid == 0) x[j] = df_mul(x[j], invd[j]);
-    __syncthreads();
-    for (int i = j + 1 + tid; i < n; i += kThreads) x[i] = df_sub(x[i], df_mul(A.get(j, i), x[j]));
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    __syncthreads();
-    if (tid == 0) x[j] = df_mul(x[j], invd[j]);
-    __syncthreads();
-    for (int i = tid; i < j; i += kThreads) x[i] = df_sub(x[i], df_mul(A.get(i, j), x[j]));
-  }
-  __syncthreads();
-}
-
 __device__ void fail_partition(const Params& p, int part, bool init) {
   const int B = p.B;
   const size_t pb = (size_t)part * B;
@@ -336,13 +204,13 @@ size_t solve_init_smem_bytes(int B, int BA) {
   return ((size_t)BA * BA + 12 * (size_t)B) * sizeof(df) + 64;
 }
 size_t solve_iter_smem_bytes(int B) {
-  return ((size_t)B * B + 12 * (size_t)B + 8) * sizeof(df) + 64;
+  return ((size_t)B * linv_ld(B) + 16 * (size_t)B + 8) * sizeof(df) + 64;
 }
 size_t solve_literal_smem_bytes(int B, int BA) {
   return ((size_t)BA * BA + 10 * (size_t)B) * sizeof(df) + 64;
 }
 
-__global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
+__global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df red[kWarps];
   const int part = blockIdx.x;
@@ -376,12 +244,11 @@ __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
   }
   __syncthreads();
   assemble(p, A, vm, nullptr, vu3, invN, p.S + (size_t)part * B * B, scr);
-  const bool ok = enough && cholesky_upper_df(A, B, invd);
+  const bool ok = enough && chol_inv_df(A, B, invd);
   if (!ok) {
     fail_partition(p, part, true);
     return;
   }
-  tri_inverse_df(A, B, invd);
   for (int b = tid; b < B; b += kThreads) {
     vt[b] = df_mulf(vmu[b], p.k[b]);
     const float mf = df_to_float(vmu[b]);
@@ -389,30 +256,17 @@ __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
     vu3[b] = df_sub(vmu[b], vmf[b]);
   }
   __syncthreads();
-  // y = L^{-1} t
-  for (int i = tid; i < B; i += kThreads) {
-    Dot2 d;
-    d.add(invd[i], vt[i]);
-    for (int j = 0; j < i; ++j) d.add(A.get(i, j), vt[j]);
-    vy[i] = d.result();
-  }
-  __syncthreads();
-  // z = L^{-T} y
-  for (int j = tid; j < B; j += kThreads) {
-    Dot2 d;
-    d.add(invd[j], vy[j]);
-    for (int i = j + 1; i < B; ++i) d.add(A.get(i, j), vy[i]);
-    vz[j] = d.result();
-  }
-  __syncthreads();
+  xtx_apply_df(A, B, invd, vt, vy, vz);  // z = (C^0)^{-1} t
   const df q = block_dot_df(vt, vz, B, red);
   const df muv = block_dot_df(vmf, vz, B, red);
   const df coff = block_dot_df(vu3, vz, B, red);
   const df n2 = block_dot_df(vmf, vmf, B, red);
-  // store L^{-1} (row-major, lower with diagonal), mean, target, solution
-  float2* X = p.Linv + (size_t)part * B * B;
-  for (int idx = tid; idx < B * B; idx += kThreads) {
-    const int i = idx / B, j = idx % B;
+  // store L^{-1} (row-major, lower with diagonal, rows padded to
+  // linv_ld(B) entries), mean, target, solution
+  const int xld = linv_ld(B);
+  float2* X = p.Linv + (size_t)part * B * xld;
+  for (int idx = tid; idx < B * xld; idx += kThreads) {
+    const int i = idx / xld, j = idx - i * xld;
     const df v = (j < i) ? A.get(i, j) : (j == i ? invd[i] : df{0.f, 0.f});
     stf(X, idx, v);
   }
@@ -453,18 +307,23 @@ __global__ void __launch_bounds__(kThreads) solve_init_kernel(Params p) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode, int pass) {
+__global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int mode, int pass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df s_y[3];
   __shared__ int s_bad;
+  __shared__ __align__(8) uint64_t s_xbar;
   const int part = blockIdx.x;
   const int tid = threadIdx.x;
   const int B = p.B;
   const size_t pb = (size_t)part * B;
   if (p.status[part] != MF_OK) return;
   if (pass > p.lines[part_line(p, part)].n_iter) return;  // the line's iterations are done
-  df* X = reinterpret_cast<df*>(smem_raw);  // L^{-1}, B x B
-  df* mom = X + (size_t)B * B;              // B + 3 moments (padded to B + 8)
+  // L^{-1} (B rows of linv_ld(B) double-floats), later the direct path's
+  // B x B matrix
+  df* X = reinterpret_cast<df*>(smem_raw);
+  float4* UP = reinterpret_cast<float4*>(X + (size_t)B * linv_ld(B));  // (g, t^{k+1}) interleaved
+  float4* YP = UP + B;
+  df* mom = reinterpret_cast<df*>(YP + B);  // B + 3 moments (padded to B + 8)
   df* U0 = mom + B + 8;                     // g
   df* U1 = U0 + B;                          // t^{k+1}
   df* U2 = U1 + B;                          // t^k - t^{k+1}
@@ -477,6 +336,32 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
   df* vmk = vmf + B;
   df* vv = vmk + B;
 
+  // this thread's band b = tid (B <= kThreads): the partition's vectors,
+  // loaded before the moment reduction so that their latency overlaps it
+  const int b = tid;
+  df mu0{0.f, 0.f}, tk{0.f, 0.f}, ztk{0.f, 0.f};
+  float mu0f = 0.f, kb = 0.f;
+  if (b < B) {
+    mu0 = ldf(p.mu0, pb + b);
+    tk = ldf(p.tprev, pb + b);
+    ztk = ldf(p.zt, pb + b);
+    mu0f = p.mu0f[pb + b];
+    kb = p.k[b];
+  }
+  const double* ds = p.dscal + (size_t)part * 4;
+  const double Nd = ds[DS_N];
+  // L^{-1} of the partition into shared memory by one bulk copy, in flight
+  // during the moment reduction
+  const bool solve = mode != SOLVE_MEAN_ONLY;
+  if (solve && tid == 0) {
+    const size_t n = (size_t)B * linv_ld(B);
+    const uint32_t bytes = (uint32_t)(n * sizeof(float2));
+    mbar_init(&s_xbar, 1);
+    mbar_fence_init();
+    mbar_arrive_expect_tx(&s_xbar, bytes);
+    bulk_load(X, p.Linv + (size_t)part * n, bytes, &s_xbar);
+  }
+
   const int K3E = k3_entries(B);
   const LineInfo& line = p.lines[part_line(p, part)];
   const int nunits = part_ncols(p, part) * line.n_rb;
@@ -487,59 +372,50 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
     mom[t] = s;
   }
   __syncthreads();
-  const double* ds = p.dscal + (size_t)part * 4;
-  const df N = df_from_double(ds[DS_N]);
+  const df N = df_from_double(Nd);
   const df invN = df_recip(N);
   const df sb = mom[0], sb2 = mom[1], sba = mom[2];
   const df bbar = df_mul(sb, invN);
   const df var = df_sub(df_mul(sb2, invN), df_mul(bbar, bbar));
-  for (int b = tid; b < B; b += kThreads) {
-    const df mu0 = ldf(p.mu0, pb + b);
-    const df mf{p.mu0f[pb + b], 0.f};
-    const df tk = ldf(p.tprev, pb + b);
+  if (b < B) {
+    const df mf{mu0f, 0.f};
     const df mk = df_sub(mu0, df_mul(bbar, tk));
-    const df t1 = df_mulf(mk, p.k[b]);
+    const df t1 = df_mulf(mk, kb);
     // g = mean(beta (x - mu0)), x - mu0 = e + (rho - 1) mu0f + (mu0f - mu0)
     df g = df_fma(sba, mf, mom[3 + b]);
     g = df_fma(sb, df_sub(mf, mu0), g);
     U0[b] = df_mul(g, invN);
     U1[b] = t1;
     U2[b] = df_sub(tk, t1);
+    UP[b] = pack_pair(U0[b], U1[b]);
     vmf[b] = mf;
     vmk[b] = mk;
   }
   if (mode == SOLVE_MEAN_ONLY) {
     __syncthreads();
-    for (int b = tid; b < B; b += kThreads) {
-      stf(p.muk, pb + b, vmk[b]);
-      stf(p.tprev, pb + b, U1[b]);
+    for (int i = tid; i < B; i += kThreads) {
+      stf(p.muk, pb + i, vmk[i]);
+      stf(p.tprev, pb + i, U1[i]);
     }
     if (tid == 0) p.dscal[(size_t)part * 4 + DS_BBAR] = df_to_double(bbar);
     return;
   }
-  const float2* Xg = p.Linv + (size_t)part * B * B;
-  for (int idx = tid; idx < B * B; idx += kThreads) X[idx] = ldf(Xg, idx);
-  __syncthreads();
-  // Y = L^{-1} [g, t]
-  for (int w = tid; w < 2 * B; w += kThreads) {
-    const int r = w / B, i = w % B;
-    const df* u = r ? U1 : U0;
-    Dot2 d;
-    for (int j = 0; j <= i; ++j) d.add(X[i * B + j], u[j]);
-    (r ? Y1 : Y0)[i] = d.result();
+  if (!__syncthreads_and(mbar_wait(&s_xbar, 0))) {
+    // the copy did not complete in time (uniform decision): record it, give
+    // the copy a second bounded wait and leave
+    if (tid == 0) p.status[part] = MF_ERR_TIMEOUT;
+    mbar_wait(&s_xbar, 0);
+    return;
   }
-  __syncthreads();
-  // Z = L^{-T} Y
-  for (int w = tid; w < 2 * B; w += kThreads) {
-    const int r = w / B, j = w % B;
-    const df* y = r ? Y1 : Y0;
-    Dot2 d;
-    for (int i = j; i < B; ++i) d.add(X[i * B + j], y[i]);
-    (r ? Z1 : Z0)[j] = d.result();
+  // [Z0, Z1] = C0^{-1} [g, t^{k+1}]
+  {
+    const float4* U[1] = {UP};
+    float4* Yv[1] = {YP};
+    df* Zv[2] = {Z0, Z1};
+    c0inv_apply<1>(X, B, U, Yv, Zv);
   }
-  __syncthreads();
   // C0^{-1} (t^k - t^{k+1}) = z(t^k) - z(t^{k+1})
-  for (int b = tid; b < B; b += kThreads) Z2[b] = df_sub(ldf(p.zt, pb + b), Z1[b]);
+  if (b < B) Z2[b] = df_sub(ztk, Z1[b]);
   __syncthreads();
   __shared__ df s_W[9];
   __shared__ df s_A3[9];
@@ -618,7 +494,7 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
   }
   if (s_bad == 2) {
     // direct path: C^{k+1} = C^0 + U M U^T assembled in double-float (into
-    // the L^{-1} buffer, no longer needed), factorised and solved
+    // the matrix region, no longer needed), factorised and solved
     const double* Sg = p.S + (size_t)part * B * B;
     const DfMat Xm{reinterpret_cast<float*>(X), B, B * B};
     const df mvar = var, mb2 = df_mul(bbar, bbar);
@@ -631,22 +507,21 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
       c = df_fma(mb2, df_mul(U2[i], U2[j]), c);
       Xm.set(i, j, c);
     }
-    for (int b = tid; b < B; b += kThreads) vv[b] = U1[b];
-    if (!cholesky_upper_df(Xm, B, Y0)) {  // Y0 holds 1/diag(U)
+    if (!chol_inv_df(Xm, B, Y0)) {  // Y0 holds 1/diag(U)
       fail_partition(p, part, false);
       return;
     }
-    chol_solve_df(Xm, B, Y0, vv);
+    xtx_apply_df(Xm, B, Y0, U1, Y1, vv);
   } else {
     const df y0 = s_y[0], y1 = s_y[1], y2 = s_y[2];
-    for (int b = tid; b < B; b += kThreads) {
-      df zy = df_mul(Z0[b], y0);
-      zy = df_fma(Z1[b], y1, zy);
-      zy = df_fma(Z2[b], y2, zy);
-      vv[b] = df_sub(Z1[b], zy);
+    for (int i = tid; i < B; i += kThreads) {
+      df zy = df_mul(Z0[i], y0);
+      zy = df_fma(Z1[i], y1, zy);
+      zy = df_fma(Z2[i], y2, zy);
+      vv[i] = df_sub(Z1[i], zy);
     }
   }
-  for (int b = tid; b < B; b += kThreads) U2[b] = df_sub(vmk[b], vmf[b]);  // mu^{k+1} - mu0f
+  for (int i = tid; i < B; i += kThreads) U2[i] = df_sub(vmk[i], vmf[i]);  // mu^{k+1} - mu0f
   __syncthreads();
   __shared__ df s_d3[3];
   {
@@ -655,19 +530,19 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
     multi_dot_df(da, db, 3, B, s_d3);
   }
   const df q = s_d3[0], muv = s_d3[1], coff = s_d3[2];
-  for (int b = tid; b < B; b += kThreads) {
-    p.vf[pb + b] = df_to_float(vv[b]);
-    stf(p.zt, pb + b, Z1[b]);
-    stf(p.tprev, pb + b, U1[b]);
-    stf(p.muk, pb + b, vmk[b]);
+  for (int i = tid; i < B; i += kThreads) {
+    p.vf[pb + i] = df_to_float(vv[i]);
+    stf(p.zt, pb + i, Z1[i]);
+    stf(p.tprev, pb + i, U1[i]);
+    stf(p.muk, pb + i, vmk[i]);
   }
   if (p.ck_vec && pass < p.ck_stages) {  // checkpoint of stage `pass`
     float2* cv = p.ck_vec + ((size_t)part * p.ck_stages + pass) * 4 * B;
-    for (int b = tid; b < B; b += kThreads) {
-      stf(cv, CKV_MU * B + b, vmk[b]);
-      stf(cv, CKV_T * B + b, U1[b]);
-      stf(cv, CKV_V * B + b, vv[b]);
-      stf(cv, CKV_G * B + b, U0[b]);
+    for (int i = tid; i < B; i += kThreads) {
+      stf(cv, CKV_MU * B + i, vmk[i]);
+      stf(cv, CKV_T * B + i, U1[i]);
+      stf(cv, CKV_V * B + i, vv[i]);
+      stf(cv, CKV_G * B + i, U0[i]);
     }
     if (tid == 0) {
       double* cs = p.ck_sc + ((size_t)part * p.ck_stages + pass) * 4;
@@ -687,7 +562,7 @@ __global__ void __launch_bounds__(kThreads) solve_iter_kernel(Params p, int mode
   }
 }
 
-__global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p, int pass) {
+__global__ void __launch_bounds__(kThreads, 4) solve_literal_kernel(Params p, int pass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df red[kWarps];
   const int part = blockIdx.x;
@@ -714,15 +589,14 @@ __global__ void __launch_bounds__(kThreads) solve_literal_kernel(Params p, int p
     u2[b] = ldf(p.tprev, pb + b);
     u3[b] = df_sub(mf, mk);
     vd[b] = df_sub(mk, mf);
-    vz[b] = u2[b];
   }
   __syncthreads();
   assemble(p, A, u1, u2, u3, invN, nullptr, vd + B);
-  if (!cholesky_upper_df(A, B, invd)) {
+  if (!chol_inv_df(A, B, invd)) {
     fail_partition(p, part, false);
     return;
   }
-  chol_solve_df(A, B, invd, vz);
+  xtx_apply_df(A, B, invd, u2, vd + B, vz);
   const df q = block_dot_df(u2, vz, B, red);
   const df muv = block_dot_df(u1, vz, B, red);
   const df coff = block_dot_df(vd, vz, B, red);
