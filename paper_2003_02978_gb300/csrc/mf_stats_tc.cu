@@ -94,27 +94,18 @@ __host__ __device__ inline TcSmem tc_layout(int B) {
   return L;
 }
 
-__device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
-  const __nv_bfloat162 lo2 = __floats2bfloat162_rn(a, b);
-  const __nv_bfloat162 hi2 = __floats2bfloat162_rn(c, d);
-  return make_uint2(*reinterpret_cast<const uint32_t*>(&lo2),
-                    *reinterpret_cast<const uint32_t*>(&hi2));
+__device__ __forceinline__ uint32_t bf162_bits(__nv_bfloat162 v) {
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
-
-// write the bf16 hi and lo parts of 4 consecutive augmented entries
-// (n0 .. n0 + 3, n0 % 4 == 0) of pixel k into the MN-major operand buffers
-__device__ __forceinline__ void put4(unsigned char* H, unsigned char* Lo, size_t kstride, int n0,
-                                     int k, float4 v) {
-  const size_t off = (size_t)(k >> 3) * kstride + (size_t)(n0 >> 3) * 128 + (k & 7) * 16 +
-                     (n0 & 7) * 2;
-  const __nv_bfloat16 hx = __float2bfloat16_rn(v.x), hy = __float2bfloat16_rn(v.y);
-  const __nv_bfloat16 hz = __float2bfloat16_rn(v.z), hw = __float2bfloat16_rn(v.w);
-  const float rx = v.x - __bfloat162float(hx), ry = v.y - __bfloat162float(hy);
-  const float rz = v.z - __bfloat162float(hz), rw = v.w - __bfloat162float(hw);
-  *reinterpret_cast<uint2*>(H + off) =
-      pack_bf16x4(__bfloat162float(hx), __bfloat162float(hy), __bfloat162float(hz),
-                  __bfloat162float(hw));
-  *reinterpret_cast<uint2*>(Lo + off) = pack_bf16x4(rx, ry, rz, rw);
+// bf16 hi and lo parts of 4 values, packed pairwise: hi = bf16(v) (round to
+// nearest), lo = bf16(v - hi), v - hi exact in float32
+__device__ __forceinline__ void split_bf16x4(float4 v, uint2& hi, uint2& lo) {
+  const float2 v01 = make_float2(v.x, v.y), v23 = make_float2(v.z, v.w);
+  const __nv_bfloat162 h01 = __float22bfloat162_rn(v01), h23 = __float22bfloat162_rn(v23);
+  const float2 r01 = __ffma2_rn(__bfloat1622float2(h01), make_float2(-1.f, -1.f), v01);
+  const float2 r23 = __ffma2_rn(__bfloat1622float2(h23), make_float2(-1.f, -1.f), v23);
+  hi = make_uint2(bf162_bits(h01), bf162_bits(h23));
+  lo = make_uint2(bf162_bits(__float22bfloat162_rn(r01)), bf162_bits(__float22bfloat162_rn(r23)));
 }
 }  // namespace
 
@@ -369,23 +360,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int e = lane & 1;
     const int slot = warp * 16 + (lane >> 1);  // pixel = K index within a stage
     const bool albedo = (p.flags & MF_ALBEDO) != 0;
-    // (item, stage) after (w, s) in this CTA's sequence, for the prefetch
-    auto next_of = [&](int& w, int& s) {
-      StatItem it;
-      int nst;
-      item_geom(w, it, nst);
-      if (++s >= nst) {
-        s = 0;
-        w += gridDim.x;
-      }
-    };
-    auto fetch = [&](int w, int s, int& m_out, float& a_out) {
+    // this lane's byte offset of group f = e + 2 j in an operand set:
+    // K group, row within the core matrix, n0 = 4 f -> j * 128 + 8 e
+    const size_t kbase = (size_t)(slot >> 3) * L.kstride + (size_t)(slot & 7) * 16 + 8 * e;
+    // mask (and alpha) of the pixel of stage s of item `it`, prefetched one
+    // stage ahead
+    auto fetch = [&](const StatItem& it, int s, int& m_out, float& a_out) {
       m_out = 0;
       a_out = 0.f;
-      if (w >= nitems) return;
-      StatItem it;
-      int nst;
-      item_geom(w, it, nst);
       const int row = it.r_beg + s * kTcRows + slot;
       if (row < it.r_end) {
         const size_t pix = (size_t)row * p.cols + it.c;
@@ -393,10 +375,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (mode == STAT_LITERAL) a_out = p.alpha[pix];
       }
     };
-    int pw = blockIdx.x, ps = 0;
-    int m_nx;
-    float a_nx;
-    fetch(pw, ps, m_nx, a_nx);
+    int m_nx = 0;
+    float a_nx = 0.f;
+    if (blockIdx.x < nitems) {
+      StatItem it0;
+      int nst0;
+      item_geom(blockIdx.x, it0, nst0);
+      if (nst0 > 0) fetch(it0, 0, m_nx, a_nx);
+    }
     int g = 0, t = 0;
     // reference direction of an item's partition, double-buffered by item:
     // the next item's is loaded into registers during the current item and
@@ -416,7 +402,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       int nst;
       item_geom(w, it, nst);
       const int part = part_of(p, it.line, it.c);
-      float* ref = s_ref + (t & 1) * (kMaxB + 4);
+      const float* ref = s_ref + (t & 1) * (kMaxB + 4);
       const float ref_next = ref_of(w + gridDim.x);
       float inv_ref2;
       if (mode == STAT_INIT) {
@@ -427,12 +413,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       } else {
         inv_ref2 = p.pscal[(size_t)part * PS_N + PS_INVMU2];
       }
-      const float4* ref4 = reinterpret_cast<const float4*>(ref);
+      // the lane's groups of the reference, in registers for the item
+      float4 rf[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int f = e + 2 * j;
+        rf[j] = f < B4 ? reinterpret_cast<const float4*>(ref)[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      // the item after this one, for the prefetch at its last stage
+      StatItem it_nx;
+      int nst_nx = 0;
+      if (w + (int)gridDim.x < nitems) item_geom(w + gridDim.x, it_nx, nst_nx);
       for (int s = 0; s < nst; ++s, ++g) {
         const int m_cur = m_nx;
         const float a_cur = a_nx;
-        next_of(pw, ps);
-        fetch(pw, ps, m_nx, a_nx);
+        if (s + 1 < nst) {
+          fetch(it, s + 1, m_nx, a_nx);
+        } else if (nst_nx > 0) {
+          fetch(it_nx, 0, m_nx, a_nx);
+        }
         if (__any_sync(0xffffffffu, failed || *(volatile int*)&s_abort)) {
           failed = true;
           continue;
@@ -448,31 +447,45 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           atomicExch(&s_abort, 1);
           continue;
         }
-        unsigned char* H = ops + (size_t)sb * L.opb;
+        unsigned char* H = ops + (size_t)sb * L.opb + kbase;
         unsigned char* Lo = H + L.lo_off;
-        const float* px = stage(fb) + (size_t)slot * B;
+        const float4* px = reinterpret_cast<const float4*>(stage(fb) + (size_t)slot * B);
         float4 x[NJ];
-        const bool fin = lds_pixel<NJ>(px, inb, e, B4, x);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&fp_empty[fb]);
-        const bool valid = inb && fin && m_cur == 0;
-        const float rho = pair_dot<NJ>(x, ref4, e, B4) * inv_ref2;
-        split_residual<NJ>(x, ref4, rho, e, B4);
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
           const int f = e + 2 * j;
-          if (f < B4) put4(H, Lo, L.kstride, 4 * f, slot, valid ? x[j] : make_float4(0.f, 0.f, 0.f, 0.f));
+          x[j] = (inb && f < B4) ? px[f] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (e == 0) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&fp_empty[fb]);
+        // every band finite <=> the dot with the (finite) reference is
+        // finite (x * 0 is NaN for x = +-Inf or NaN)
+        const float dot = pair_dot2<NJ>(x, rf);
+        const bool valid = inb && isfinite(dot) && m_cur == 0;
+        const float rho = dot * inv_ref2;
+        split_residual2<NJ>(x, rf, rho);
+        float4 aug = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
           float bcf = 0.f;
-          if (mode == STAT_LITERAL && valid) {
+          if (mode == STAT_LITERAL) {
             const float r = albedo ? rho : 1.f;
             bcf = r > 0.f ? -(r * a_cur) : 0.f;
           }
-          put4(H, Lo, L.kstride, B, slot,
-               valid ? make_float4(rho - 1.f, bcf, 1.f, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f));
-          for (int n0 = BA; n0 < NP; n0 += 4)
-            put4(H, Lo, L.kstride, n0, slot, make_float4(0.f, 0.f, 0.f, 0.f));
+          aug = make_float4(rho - 1.f, bcf, 1.f, 0.f);
+        }
+        // groups f = e + 2 j of the augmented vector [e, rho - 1, bcf, 1, 0 ..]
+        // up to NP: bands, the augmentation at f = B4, zeros after it
+#pragma unroll
+        for (int j = 0; j < NJ + 2; ++j) {
+          const int f = e + 2 * j;
+          if (4 * f >= NP) break;
+          float4 v;
+          if (j < NJ && f < B4) v = valid ? x[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          else v = f == B4 ? aug : make_float4(0.f, 0.f, 0.f, 0.f);
+          uint2 hi, lo;
+          split_bf16x4(v, hi, lo);
+          *reinterpret_cast<uint2*>(H + (size_t)j * 128) = hi;
+          *reinterpret_cast<uint2*>(Lo + (size_t)j * 128) = lo;
         }
         fence_proxy_async_smem();  // operand writes -> tensor core (async proxy)
         __syncwarp();
