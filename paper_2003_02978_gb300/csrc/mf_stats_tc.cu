@@ -323,24 +323,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_after();
         const uint32_t acc = tmem + lanes + (uint32_t)(sb * L.accw);
         const bool last = s == nst - 1;
-        for (int c0 = 0; c0 < NP; c0 += 8) {
-          uint32_t hh[8], hl[8], qs[8];
-          tmem_ld8(acc + (uint32_t)c0, hh);
-          tmem_ld8(acc + (uint32_t)(NP + c0), hl);
-          if (s > 0) tmem_ld8(qsum + (uint32_t)c0, qs);
+        // batches of 32 columns (16-column loads of H^T H + L^T L, H^T L
+        // and the running sum, one wait per batch)
+        for (int c0 = 0; c0 < NP; c0 += 32) {
+          const bool two = c0 + 16 < NP;
+          uint32_t hh[32], hl[32], qs[32];
+          tmem_ld16(acc + (uint32_t)c0, hh);
+          tmem_ld16(acc + (uint32_t)(NP + c0), hl);
+          if (s > 0) tmem_ld16(qsum + (uint32_t)c0, qs);
+          if (two) {
+            tmem_ld16(acc + (uint32_t)(c0 + 16), hh + 16);
+            tmem_ld16(acc + (uint32_t)(NP + c0 + 16), hl + 16);
+            if (s > 0) tmem_ld16(qsum + (uint32_t)(c0 + 16), qs + 16);
+          }
           tmem_wait_ld();
+          tmem_regs_after_wait<32>(hh);
+          tmem_regs_after_wait<32>(hl);
+          if (s > 0) tmem_regs_after_wait<32>(qs);
           // Q = (H^T H + L^T L) / 2 + H^T L  (+ the running sum)
-          float q[8];
+          float q[32];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < 32; ++k) {
             q[k] = fmaf(0.5f, __uint_as_float(hh[k]), __uint_as_float(hl[k]));
             if (s > 0) q[k] += __uint_as_float(qs[k]);
           }
           if (!last) {
-            tmem_st8(qsum + (uint32_t)c0, q);
+            tmem_st16(qsum + (uint32_t)c0, q);
+            if (two) tmem_st16(qsum + (uint32_t)(c0 + 16), q + 16);
           } else if (m < BA) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < 32; ++k) {
               const int j = c0 + k;
               const int bj = j >> 2, v = j & 3;
               if (j >= BA) continue;
