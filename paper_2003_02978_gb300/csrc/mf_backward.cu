@@ -277,13 +277,14 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     float4 x[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) x[j] = reinterpret_cast<const float4*>(px)[goff[j]];
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[sq]);
-
     float4 ref[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) ref[j] = mu_s[2 * j];
     const float rho_raw = pair_dot2<NJ>(x, ref);
+    // every lane's x is in registers (the dot consumed it): only now release
+    // the stage to the next TMA copy, which must not overtake a pending load
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[sq]);
     const float rho = rho_raw * invm2;
     split_residual2<NJ>(x, ref, rho);  // x <- e = x - rho mu0f
 #pragma unroll

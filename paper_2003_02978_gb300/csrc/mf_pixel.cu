@@ -211,13 +211,14 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
       for (int j = 0; j < NJ; ++j) f = f && finite4(x[j]);
       fin_exact = __shfl_xor_sync(0xffffffffu, (int)f, 1) && f;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[sq]);
-
     float4 ref[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) ref[j] = mu_s[2 * j];
     const float rho_raw = pair_dot2<NJ>(x, ref);
+    // every lane's x is in registers (the dot consumed it): only now release
+    // the stage to the next TMA copy, which must not overtake a pending load
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[sq]);
     const float rho = rho_raw * invmu2;
     split_residual2<NJ>(x, ref, rho);
 #pragma unroll

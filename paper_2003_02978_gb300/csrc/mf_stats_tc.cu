@@ -15,9 +15,9 @@
 //   D[:, 0 : 2 NP]  = H^T [H | L]       (M = 128, N = 2 NP)
 //   D[:, 0 : NP]   += L^T L             (M = 128, N = NP)
 // where NP = B + 4 rounded up to 16; an operand set holds H and L side by
-// side along N (MN-major core matrices), and an A operand is the first 128
-// columns from H's or L's start (the columns past NP are garbage rows of D
-// that the epilogue ignores).  D accumulates in float32 in tensor memory;
+// side along N (MN-major core matrices), followed by 128 - NP zero columns,
+// and an A operand is the first 128 columns from H's or L's start (the
+// columns past NP give rows of D that the epilogue ignores).  D accumulates in float32 in tensor memory;
 // the epilogue forms Q = (H^T H + L^T L) / 2 + H^T L, and G = Q + Q^T is
 // completed where the per-item moments are summed (each moment entry is
 // stored as the pair (Q_ab, Q_ba), read as their sum).
@@ -60,9 +60,10 @@ constexpr int kMaxFpStages = 3;
 struct TcSmem {
   int NP;                  // N: augmented width rounded up to 16
   int nfp;                 // float32 stages in flight (3, or 2 for wide windows)
-  size_t opb;              // one operand set: [H | L], 2 NP x 128 bf16
+  size_t opb;              // one operand set: 16 K groups of [H | L | zeros]
   size_t kstride;          // bytes between core matrices along K (8 pixels)
   size_t lo_off;           // L's first core matrix relative to H's
+  size_t pad_off, pad_bytes;  // zero columns after L in each K group
   int accw;                // tensor-memory columns of one stage accumulator (2 NP, 32-aligned)
   size_t stage_bytes;      // float32 stage: 128 rows x B
   size_t ops_off, stage_off, ref_off, bar_off, slot_off, total;
@@ -74,12 +75,15 @@ __host__ __device__ inline TcSmem tc_layout_n(int B, int nfp) {
   L.nfp = nfp;
   L.accw = (2 * L.NP + 31) / 32 * 32;  // accumulators at 0 and accw, running sum at 2 accw
   L.lo_off = (size_t)(L.NP / 8) * 128;
-  L.kstride = 2 * L.lo_off;
+  // an A operand is 128 columns (M) from H's or L's start: from L's start it
+  // runs 128 - NP columns past L, into zero columns that close the K group,
+  // so that every operand byte the tensor core reads is written data
+  L.pad_off = 2 * L.lo_off;
+  L.pad_bytes = (size_t)((kTcM - L.NP) / 8) * 128;
+  L.kstride = L.pad_off + L.pad_bytes;
   L.opb = L.kstride * (kTcRows / 8);
   L.stage_bytes = (size_t)kTcRows * B * sizeof(float);
-  // two operand sets, then the float32 stages: an A operand read from L's
-  // start in the last K group of set 1 runs 2048 - 16 NP bytes (NP >= 80)
-  // past the set, into the first stage, still inside the allocation
+  // two operand sets, then the float32 stages
   L.ops_off = 0;
   L.stage_off = L.ops_off + 2 * L.opb;
   L.ref_off = L.stage_off + nfp * L.stage_bytes;
@@ -166,8 +170,15 @@ __global__ void pilot_kernel(Params p) {
     if (lane + 32 * q < p.B) p.pilot[(size_t)part * p.B + lane + 32 * q] = sum[q] * inv;
 }
 
-// named barrier among the 8 converter warps
-__device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// named barrier 1 among the converter warps.  It follows code where only
+// some lanes of a warp store (the next item's reference): the warp is
+// reconverged first, and the barrier is the non-aligned form, which counts
+// every thread however the warp arrives (the aligned bar.sync needs a
+// converged warp, else the count can complete before every warp is in)
+__device__ __forceinline__ void conv_bar() {
+  __syncwarp();
+  asm volatile("barrier.sync 1, %0;" ::"n"(kTcConv) : "memory");
+}
 
 template <int NJ>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -215,6 +226,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tmem_alloc(tslot, kTmemCols);
     tmem_relinquish();
   }
+  // the zero columns of both operand sets (never written again)
+  for (int i = tid; i < 2 * (kTcRows / 8) * (int)(L.pad_bytes / 16); i += kTcThreads) {
+    const int per = (int)(L.pad_bytes / 16);
+    const int kg = i / per, r = i - kg * per;  // K group (over both sets), 16-byte word
+    *reinterpret_cast<uint4*>(ops + (size_t)kg * L.kstride + L.pad_off + (size_t)r * 16) =
+        make_uint4(0u, 0u, 0u, 0u);
+  }
+  fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -468,11 +487,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int f = e + 2 * j;
           x[j] = (inb && f < B4) ? px[f] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&fp_empty[fb]);
         // every band finite <=> the dot with the (finite) reference is
         // finite (x * 0 is NaN for x = +-Inf or NaN)
         const float dot = pair_dot2<NJ>(x, rf);
+        // every lane's x is in registers (the dot consumed it): only now
+        // release the float32 stage to the next TMA copy, which must not
+        // overtake a pending load
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&fp_empty[fb]);
         const bool valid = inb && isfinite(dot) && m_cur == 0;
         const float rho = dot * inv_ref2;
         split_residual2<NJ>(x, rf, rho);

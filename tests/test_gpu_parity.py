@@ -280,6 +280,33 @@ def test_bf16split_background_error():
         assert np.linalg.norm(cov[c] - C) / np.linalg.norm(C) < 1e-5
 
 
+@pytest.mark.parametrize("rows,cols,bands", [(2600, 160, 72), (2600, 160, 64), (1500, 320, 68)])
+def test_bf16split_background_every_partition(rows, cols, bands):
+    """C^0 and mu^0 of the tensor-core form for every partition of workloads
+    whose statistics items span several 128-row stages and several items per
+    CTA (the pipelined path: float32 stages refilled by TMA while converter
+    warps read them, operand sets reused every other stage), against the FP64
+    oracle's mean and covariance of the valid pixels."""
+    import paper_2003_02978_gb300 as mfg
+    sc = make_scene(rows, cols, bands, n_plumes=4, plume_sigma=(3.0, 8.0),
+                    plume_peak=(500.0, 3000.0), mask_frac=0.05, seed=rows + cols + bands)
+    plan = mfg.Plan(rows, cols, bands, precision=BF16SPLIT)
+    plan.retrieve(sc.cube.cuda(), sc.k, 1e-3, 1e-9, 0, mask=sc.mask.cuda())
+    torch.cuda.synchronize()
+    assert np.all(plan.status() == 0)
+    mu, cov = (t.cpu().numpy() for t in plan.background())
+    cube = sc.cube.numpy()
+    valid = oracle.valid_pixels(cube, sc.mask.numpy())
+    errs = []
+    for c in range(cols):
+        X = cube[valid[:, c], c].astype(np.float64)
+        m = oracle.mean_vector(X)
+        C = oracle.covariance_about(X - m)
+        np.testing.assert_allclose(mu[c], m, rtol=1e-6, atol=0)
+        errs.append(np.linalg.norm(cov[c] - C) / np.linalg.norm(C))
+    assert max(errs) < 1e-5, (int(np.argmax(errs)), max(errs))
+
+
 def test_bf16split_flightline_sampled():
     import paper_2003_02978_gb300 as mfg
     sc, prm = workload_scene("flightline-4000x598x72", seed=0, device="cuda")
