@@ -331,6 +331,15 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   // 1024 rows in the tensor-core form (float32 sums in tensor memory) and
   // 2048 otherwise.  Every line is split evenly into whole blocks / chunks.
   p.n_ct = (p.cols + mf::kTileCols - 1) / mf::kTileCols;
+  {
+    // the share of the cube that a pixel pass leaves in L2 for the next one:
+    // about 3/4 of the L2 (the rest holds the pass's writes and moments)
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const double cube = (double)p.rows * p.cols * (d->band_hi - d->band_lo) * sizeof(float);
+    p.l2_keep = cube > 0 ? (float)std::min(1.0, 0.75 * l2 / cube) : 0.f;
+  }
   int hp = tune && tune->pixel_rows > 0 ? tune->pixel_rows : env_int("MF_RB_ROWS", 0);
   if (hp <= 0) {
     const long waves = (long)mf::pixel_ctas_per_sm(pl->nj) * pl->num_sms;

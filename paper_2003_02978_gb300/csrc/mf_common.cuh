@@ -69,6 +69,8 @@ struct Params {
   int n_lines, n_items, n_blocks;  // lines; statistics items; pixel CTAs
   uint32_t flags;
   float eps;
+  float l2_keep;          // pixel passes: fraction of each CTA's stages read last that
+                          // are kept in L2 for the next pass (it walks the rows back)
   const LineInfo* lines;  // device, n_lines
   // caller buffers
   const float* cube;

@@ -89,6 +89,11 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
   const int r_end = min(line.row0 + line.rows, r_beg + line.rb_rows);
   const int nst = (r_end - r_beg + kStageRows - 1) / kStageRows;
   const uint32_t box_bytes = (uint32_t)(kStageRows * kTileCols * B * sizeof(float));
+  // first row of the i-th stage processed: odd passes walk the rows
+  // backwards, so that a pass starts on the rows the previous pass read
+  // last, which are still in L2 (the cube is larger than L2)
+  const bool backwards = (pass & 1) != 0;
+  auto stage_row = [&](int i) { return r_beg + (backwards ? nst - 1 - i : i) * kStageRows; };
 
   if (tid == 0) {
     s_abort = 0;
@@ -100,10 +105,13 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
   }
   __syncthreads();
   int issued[kPixStages] = {0};  // thread 0: copies issued per stage buffer
+  // the stages read last are kept in L2 for the next pass, the rest may go
+  const int n_keep = (int)(p.l2_keep * (float)nst);
+  const uint64_t pol_keep = l2_policy_evict_last(), pol_stream = l2_policy_evict_first();
   auto load = [&](int q, int i) {
     mbar_arrive_expect_tx(&full[q], box_bytes);
-    tma_load_3d(smem_raw + q * L.stage_bytes, &map, p.band_lo, c0t, r_beg + i * kStageRows,
-                &full[q]);
+    tma_load_3d_hint(smem_raw + q * L.stage_bytes, &map, p.band_lo, c0t, stage_row(i), &full[q],
+                     i >= nst - n_keep ? pol_keep : pol_stream);
     ++issued[q];
   };
   if (tid == 0) {
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
 
   // alpha (previous estimate or alpha_init) and the mask of stage i
   auto fetch = [&](int i, float& a_out, int& m_out) {
-    const int row = r_beg + i * kStageRows + warp;
+    const int row = stage_row(i) + warp;
     a_out = 0.f;
     m_out = 0;
     if (i < nst && row < r_end && col_ok) {
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
       atomicExch(&s_abort, 1);
       break;
     }
-    const int row = r_beg + i * kStageRows + warp;
+    const int row = stage_row(i) + warp;
     const bool inb = row < r_end && col_ok;
     const float* px = reinterpret_cast<const float*>(smem_raw + sq * L.stage_bytes) +
                       (size_t)(warp * kTileCols + s_col) * B;
