@@ -162,6 +162,13 @@ __global__ void __launch_bounds__(kBwThreads, 1)
   const int r_end = min(line.rows, r_beg + line.rb_rows);
   const int nst = (r_end - r_beg + kStageRows - 1) / kStageRows;
   const uint32_t box_bytes = (uint32_t)(kStageRows * kTileCols * B * sizeof(float));
+  // pass B walks the rows backwards, so that it starts on the rows pass A
+  // read last (kept in L2 with an evict-last policy); the next stage's pass
+  // A then starts on the rows pass B read last
+  const bool backwards = phase == 1;
+  auto stage_row = [&](int i) { return r_beg + (backwards ? nst - 1 - i : i) * kStageRows; };
+  const int n_keep = (int)(p.l2_keep * (float)nst);
+  const uint64_t pol_keep = l2_policy_evict_last(), pol_stream = l2_policy_evict_first();
   const int n = b.n_iter;
   const int S = p.ck_stages;
   const size_t npix = (size_t)p.rows * p.cols;
@@ -178,8 +185,8 @@ __global__ void __launch_bounds__(kBwThreads, 1)
   int issued[kBwStages] = {0};
   auto load = [&](int q, int i) {
     mbar_arrive_expect_tx(&full[q], box_bytes);
-    tma_load_3d(smem_raw + q * L.stage_bytes, &map, p.band_lo, c0t, r_beg + i * kStageRows,
-                &full[q]);
+    tma_load_3d_hint(smem_raw + q * L.stage_bytes, &map, p.band_lo, c0t, stage_row(i), &full[q],
+                     i >= nst - n_keep ? pol_keep : pol_stream);
     ++issued[q];
   };
   if (tid == 0) {
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
       else
         atomicExch(&s_abort, 1);
     }
-    const int row = r_beg + i * kStageRows + warp;
+    const int row = stage_row(i) + warp;
     const bool inb = row < r_end && col_ok;
     const size_t pix = (size_t)(line.row0 + row) * p.cols + c;
     float ak = 0.f, ap = 0.f, abin = 0.f;
