@@ -7,7 +7,10 @@ neither side ever supplies the other's inputs.
 Generative model (linearised Beer-Lambert forward model, Eq. (1) of Foote et
 al. 2020, with the scene structure of Sec. II-F/II-G and Sec. III):
 
-  x_i = a_i (mu_c + z_i) (.) (1 + alpha_i k)
+  x_i = a_i (mu_c + z_i) (.) (1 + alpha_i k)         (forward_model="linear")
+  x_i = a_i (mu_c + z_i) (.) exp(alpha_i k)           (forward_model="exp": the
+        Beer-Lambert law itself, Sec. II-A, before the first-order expansion
+        that Eq. (1) makes; k <= 0, so exp(alpha k) is the transmittance)
   z_i ~ N(0, C_bg),  C_bg = U U^T + diag(sigma^2),  sigma_b = mu_b / SNR_b
   a_i ~ lognormal(0, albedo_sigma)           per-pixel albedo
   k   = -sum_j A_j exp(-(wl - c_j)^2 / 2 s_j^2), min_b k_b = -1e-4 (ppm m)^-1
@@ -117,9 +120,14 @@ def make_scene(rows: int, cols: int, bands: int = 72, *, n_plumes: int = 1,
                plume_sigma=(3.0, 3.0), plume_peak=(2000.0, 2000.0), mask_frac=0.0,
                mask_col_frac=None, cond: float = 1e4, snr=(100.0, 500.0),
                albedo_sigma: float = 0.2, seed: int = 0, device="cpu",
-               nan_masked: bool = False, keep_truth: bool = True) -> Scene:
+               nan_masked: bool = False, keep_truth: bool = True,
+               forward_model: str = "linear") -> Scene:
     """Draw one scene.  ``device`` is where the cube is generated (torch
-    Philox on CUDA, torch CPU generator otherwise)."""
+    Philox on CUDA, torch CPU generator otherwise).  ``forward_model``:
+    "linear" (first-order Beer-Lambert, the model the filter assumes) or
+    "exp" (the unlinearised Beer-Lambert transmittance)."""
+    if forward_model not in ("linear", "exp"):
+        raise ValueError("forward_model must be 'linear' or 'exp'")
     wl = wavelengths(bands)
     k = absorption_spectrum(wl, seed=seed)
     mu_bg, U, sigma = background_model(wl, cond=cond, snr=snr, seed=seed)
@@ -150,7 +158,9 @@ def make_scene(rows: int, cols: int, bands: int = 72, *, n_plumes: int = 1,
         a = torch.exp(albedo_sigma * torch.randn((n, cols), generator=g, device=dev, dtype=f32))
         albedo[r0:r1] = a
         bg = mu_t[None, None, :] * gain_t[None, :, None] + z
-        cube[r0:r1] = a[:, :, None] * bg * (1.0 + alpha_t[r0:r1, :, None] * k_t[None, None, :])
+        ak = alpha_t[r0:r1, :, None] * k_t[None, None, :]
+        trans = torch.exp(ak) if forward_model == "exp" else 1.0 + ak
+        cube[r0:r1] = a[:, :, None] * bg * trans
     mask = None
     if mask_frac or mask_col_frac is not None:
         if mask_col_frac is not None:
@@ -166,7 +176,8 @@ def make_scene(rows: int, cols: int, bands: int = 72, *, n_plumes: int = 1,
     return Scene(cube=cube, k=k, mask=mask, alpha_true=alpha if keep_truth else None,
                  albedo=albedo.cpu().numpy() if keep_truth and rows * cols <= (1 << 24) else None,
                  mu_bg=mu_bg, C_bg=C_bg, wl=wl,
-                 meta=dict(rows=rows, cols=cols, bands=bands, seed=seed, cond=cond))
+                 meta=dict(rows=rows, cols=cols, bands=bands, seed=seed, cond=cond,
+                           forward_model=forward_model))
 
 
 # Named workloads (shapes of the five configurations the benchmarks and the
@@ -183,6 +194,11 @@ WORKLOADS = {
                                    plume_sigma=(3.0, 15.0), plume_peak=(500.0, 5000.0),
                                    mask_frac=0.05, lam=1e-3, eps=1e-9, n_iter=10, cond=1e7,
                                    snr=(100.0, 500.0)),
+    # the flightline with the unlinearised (exponential) Beer-Lambert forward model
+    "flightline-exp-4000x598x72": dict(rows=4000, cols=598, bands=72, n_plumes=20,
+                                       plume_sigma=(3.0, 15.0), plume_peak=(500.0, 5000.0),
+                                       mask_frac=0.05, lam=1e-3, eps=1e-9, n_iter=10,
+                                       forward_model="exp"),
     "diff-8000x598x72": dict(rows=8000, cols=598, bands=72, n_plumes=20,
                              plume_sigma=(3.0, 15.0), plume_peak=(500.0, 5000.0),
                              mask_frac=0.05, lam=1e-3, eps=1e-9, n_iter=10),

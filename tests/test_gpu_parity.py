@@ -307,6 +307,17 @@ def test_bf16split_background_every_partition(rows, cols, bands):
     assert max(errs) < 1e-5, (int(np.argmax(errs)), max(errs))
 
 
+@pytest.mark.parametrize("precision", [0, BF16SPLIT])
+def test_exp_forward_model(precision):
+    """A scene drawn with the unlinearised Beer-Lambert law (Sec. II-A): the
+    filter's model is the first-order expansion, but the retrieval is still
+    the same computation, so parity with the oracle holds on these inputs."""
+    sc = make_scene(700, 12, 72, n_plumes=3, plume_sigma=(3.0, 6.0),
+                    plume_peak=(1000.0, 5000.0), mask_frac=0.03, seed=21, forward_model="exp")
+    compare(sc.cube.numpy(), sc.k, 1e-3, 1e-9, 10, mask=sc.mask.numpy(), precision=precision,
+            tol=TOL_BF16SPLIT if precision else TOL_FP32)
+
+
 def test_bf16split_flightline_sampled():
     import paper_2003_02978_gb300 as mfg
     sc, prm = workload_scene("flightline-4000x598x72", seed=0, device="cuda")
