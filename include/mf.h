@@ -121,6 +121,25 @@ mf_status mf_retrieve_host(mf_plan_t plan, const float* cube, const float* k, do
                            double eps, int32_t n_iter, const uint8_t* mask,
                            float* alpha_out, void* stream);
 
+/* mf_retrieve (no alpha_init, no albedo output) that also writes the
+ * objective of every iterate, the energy whose decrease Fig. 5 tracks (Sec.
+ * III-B): for iterate k = 0..n_iter of partition j,
+ *   energy_out[j * (n_iter + 1) + k] = sum_i f_i(alpha_i^k),
+ *   f_i(a) = d^T (C^k)^-1 d + 2 pen_i r_i a,  d = (L_i - mu^k) - r_i a t^k,
+ * over the partition's valid pixels: the bracket of Eq. (8) in the form the
+ * shrinkage step of Fig. 1 minimises exactly (pen_i = lambda w_i^k, 0 at
+ * k = 0; alpha^0 is the unclamped initial estimate), with mu^k, C^k, t^k of
+ * iterate k.  The quadratic term is summed in closed form per partition,
+ * N tr((C^k)^-1 S^k) with S^k the scatter of the pixels about mu^k.
+ *   energy_out  device, (P, n_iter + 1) float64, 8-byte aligned; NaN for a
+ *               partition that fails, and for an iterate whose covariance
+ *               took the direct (non-Woodbury) factorisation
+ * Single-line plans, fused schedule (MF_LITERAL: MF_ERR_UNSUPPORTED).  Runs
+ * the kernels directly (no graph).  Allocates nothing, does not synchronise. */
+mf_status mf_retrieve_energy(mf_plan_t plan, const float* cube, const float* k, double lambda,
+                             double eps, int32_t n_iter, const uint8_t* mask, float* alpha_out,
+                             double* energy_out, void* stream);
+
 /* Batched form: many flightlines of uneven length in one retrieval.  The
  * lines are stacked along rows in one BIP cube: line l is rows
  * [line_rows[0] + ... + line_rows[l-1], ... + line_rows[l]) and desc->rows is

@@ -52,6 +52,11 @@ R9  r_i <= 0 (impossible for positive radiance): alpha_i = 0 and beta_i = 0,
     the pixel still counts in the statistics.
 R10 Partitions: groups of ``col_group`` adjacent detector columns, the
     remainder forming a last smaller group (Sec. II-E).
+R17 The energy tracked in Fig. 5 is the sum over the partition's valid pixels
+    of the bracket of Eq. (8) in the form the shrinkage step minimises exactly
+    (R4, with the penalty of R5), evaluated at each iterate with that
+    iterate's mu^k, C^k, t^k and weights; iterate 0 is the unclamped initial
+    estimate without a penalty.
 
 Parity pins for every function live in ``tests/test_oracle_pins.py``.
 """
@@ -246,6 +251,47 @@ def retrieve(cube, s, lam=1.0, eps=1e-9, n_iter=10, mask=None, band_lo=0, band_h
             status[pi] = STATUS_NOT_SPD
         alpha[:, c0:c1] = blk
     return alpha, status
+
+
+def partition_energy(X, s, lam=1.0, eps=1e-9, n_iter=10, flags=ALBEDO | SPARSE):
+    """Objective of every iterate of Fig. 1 on one partition (the energy of
+    Fig. 5, Sec. III-B): E^k = sum_i f_i(alpha_i^k), k = 0..n_iter, with the
+    per-pixel objective f of R4 at iterate k's mu^k, C^k, t^k and pen^k
+    (``pixel_energy``), summed over the partition's pixels.  Iterate 0 is the
+    unclamped initial estimate with no penalty (R3: the clamp feeds the first
+    reweighting, it is not part of the initial estimate).  Reading R17."""
+    X = np.asarray(X, dtype=np.float64)
+    _, tr = retrieve_partition(X, s, lam, eps, n_iter, flags, trace=True)
+    r = tr["r"]
+    E = np.empty(n_iter + 1)
+    for k in range(n_iter + 1):
+        a = tr["alpha"][k]
+        ra = np.where(r > 0, r * a, 0.0)
+        D = (X - tr["mu"][k]) - ra[:, None] * tr["t"][k][None, :]
+        Z = spd_solve(tr["C"][k], D.T)                 # C^-1 d_i, column per pixel
+        E[k] = float(np.sum(D.T * Z) + 2.0 * np.sum(tr["pen"][k] * ra))
+    return E
+
+
+def retrieve_energy(cube, s, lam=1.0, eps=1e-9, n_iter=10, mask=None, band_lo=0, band_hi=None,
+                    col_group=1, flags=ALBEDO | SPARSE):
+    """``partition_energy`` for every partition of a cube (R10): (P, n_iter + 1)
+    float64, NaN rows for partitions that fail (R8)."""
+    cube = np.asarray(cube)
+    rows, cols, bt = cube.shape
+    if band_hi is None:
+        band_hi = bt
+    win = cube[:, :, band_lo:band_hi]
+    ok = valid_pixels(win, mask)
+    parts = partitions(cols, col_group)
+    out = np.full((len(parts), n_iter + 1), np.nan)
+    for pi, (c0, c1) in enumerate(parts):
+        X = win[:, c0:c1][ok[:, c0:c1]].astype(np.float64)
+        try:
+            out[pi] = partition_energy(X, s, lam, eps, n_iter, flags)
+        except NotSPD:
+            pass
+    return out
 
 
 def amplification(X, s, lam=1.0, eps=1e-9, n_iter=10, flags=ALBEDO | SPARSE, alpha_init=None):

@@ -153,6 +153,22 @@ class Plan:
     def ckpt_bytes(self, n_iter, cube_grad=False) -> int:
         return int(lib().mf_ckpt_bytes(self._h, int(n_iter), int(bool(cube_grad))))
 
+    def retrieve_energy(self, cube, k, lam, eps, n_iter, mask=None, out=None, stream=None):
+        """Retrieval that also returns the objective of every iterate (the
+        energy of Fig. 5): (alpha (rows, cols) float32, energy (P, n_iter + 1)
+        float64), both CUDA tensors (mf_retrieve_energy)."""
+        s = self.shape
+        self._check_cube(cube)
+        k = torch.as_tensor(k, dtype=torch.float32, device=cube.device).contiguous()
+        if out is None:
+            out = torch.empty((s.rows, s.cols), dtype=torch.float32, device=cube.device)
+        energy = torch.empty((self.P, int(n_iter) + 1), dtype=torch.float64, device=cube.device)
+        check(lib().mf_retrieve_energy(self._h, _ptr(cube), _ptr(k), float(lam), float(eps),
+                                       int(n_iter), _ptr(mask), _ptr(out), _ptr(energy),
+                                       _stream_handle(stream)),
+              "mf_retrieve_energy")
+        return out, energy
+
     def retrieve_train(self, cube, k, lam, eps, n_iter, mask=None, cube_grad=False, out=None,
                        ckpt=None, stream=None):
         """Checkpointed retrieval for the backward pass.  Returns (alpha,

@@ -74,6 +74,9 @@ def lib() -> ctypes.CDLL:
     L.mf_retrieve_backward.restype = c_int
     L.mf_num_lines.argtypes = [c_void_p]
     L.mf_num_lines.restype = c_int32
+    L.mf_retrieve_energy.argtypes = [c_void_p, fp, fp, c_double, c_double, c_int32, fp, fp, fp,
+                                     c_void_p]
+    L.mf_retrieve_energy.restype = c_int
     L.mf_retrieve_batched.argtypes = [c_void_p, fp, fp, POINTER(c_double), c_double,
                                       POINTER(c_int32), fp, fp, c_void_p]
     L.mf_retrieve_batched.restype = c_int

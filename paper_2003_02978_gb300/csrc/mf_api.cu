@@ -496,6 +496,8 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
     p.ck_vec = ck->ck_vec;
     p.ck_sc = ck->ck_sc;
     p.ck_stages = ck->ck_stages;
+    p.energy = ck->energy;
+    p.energy_stride = ck->energy_stride;
   }
   const bool literal = (p.flags & MF_LITERAL) != 0;
   if (cube != pl->map_cube) {
@@ -528,6 +530,7 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
   MF_CUDA(cudaStreamIsCapturing(s, &cs));
   if (pl->profile || !pl->use_graph || ck || cs != cudaStreamCaptureStatusNone) {
     enqueue(s);
+    if (p.energy) mf::energy_final_launch(s, p, n_iter_max);
     MF_CUDA(cudaGetLastError());
   } else {
     const mf_plan_s::GraphKey key{{cube, k, mask, alpha_init, alpha_out, albedo_out},
@@ -630,6 +633,29 @@ mf_status mf_retrieve(mf_plan_t pl, const float* cube, const float* k, double la
   st = upload_lines(pl, &lambda, &n_iter, s);
   if (st != MF_OK) return st;
   return run_retrieval(pl, cube, k, eps, n_iter, mask, alpha_init, alpha_out, albedo_out, s);
+}
+
+mf_status mf_retrieve_energy(mf_plan_t pl, const float* cube, const float* k, double lambda,
+                             double eps, int32_t n_iter, const uint8_t* mask, float* alpha_out,
+                             double* energy_out, void* stream) {
+  g_last_error.clear();
+  if (!pl) return fail(MF_ERR_INVALID_ARG, "null plan");
+  if (!cube || !k || !alpha_out || !energy_out)
+    return fail(MF_ERR_INVALID_ARG, "null cube, k, alpha_out or energy_out");
+  if ((reinterpret_cast<uintptr_t>(energy_out) & 7) != 0)
+    return fail(MF_ERR_INVALID_ARG, "energy_out must be 8-byte aligned");
+  if (pl->n_lines != 1) return fail(MF_ERR_UNSUPPORTED, "the energy output takes one line");
+  if (pl->prm.flags & MF_LITERAL)
+    return fail(MF_ERR_UNSUPPORTED, "the energy output follows the fused schedule (no MF_LITERAL)");
+  mf_status st = check_scalars(lambda, eps, n_iter);
+  if (st != MF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = upload_lines(pl, &lambda, &n_iter, s);
+  if (st != MF_OK) return st;
+  mf::Params extra{};
+  extra.energy = energy_out;
+  extra.energy_stride = n_iter + 1;
+  return run_retrieval(pl, cube, k, eps, n_iter, mask, nullptr, alpha_out, nullptr, s, &extra);
 }
 
 mf_status mf_retrieve_batched(mf_plan_t pl, const float* cube, const float* k,

@@ -71,6 +71,8 @@ struct Params {
   float eps;
   float l2_keep;          // pixel passes: fraction of each CTA's stages read last that
                           // are kept in L2 for the next pass (it walks the rows back)
+  double* energy;         // optional: (P, energy_stride) objective per iterate (null = off)
+  int energy_stride;      // n_iter + 1
   const LineInfo* lines;  // device, n_lines
   // caller buffers
   const float* cube;
@@ -137,6 +139,8 @@ __host__ __device__ inline int k1_entries(int BA) {
   const int nb = BA / 4;
   return nb * (nb + 1) / 2 * 16;
 }
+// per pixel-kernel CTA and column: sum beta, sum beta^2, sum beta (rho - 1),
+// sum beta e (B entries), and the pass's per-pixel energy terms (when asked)
 __host__ __device__ inline int k3_entries(int B) { return B + 4; }
 
 // partition of column c of line l; its line; its first column; its width
@@ -235,6 +239,7 @@ cudaError_t stats_tc_set_attributes(int nj, size_t smem);
 void stats_tc_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
                      const Params& p, int mode, int pass);
 void pilot_launch(cudaStream_t s, const Params& p);
+void energy_final_launch(cudaStream_t s, const Params& p, int k);
 // backward pass (mf_backward.cu)
 size_t bwd_pixel_smem_bytes(int B, int nj);
 size_t bwd_solve_smem_bytes(int B);

@@ -170,6 +170,11 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
 #pragma unroll
   for (int j = 0; j < NJ; ++j) g[j] = make_float4(0.f, 0.f, 0.f, 0.f);
   float sb = 0.f, sb2 = 0.f, sba = 0.f;
+  // per-pixel terms of the objective (Eq. (8) as the shrinkage step
+  // minimises it) at this pass's iterate, when the energy is asked for:
+  // f_i(a) - (x_i - mu)^T C^-1 (x_i - mu) = -2 r a p + r^2 a^2 q + 2 pen r a
+  const bool want_energy = p.energy != nullptr;
+  float en = 0.f;
 
   // alpha (previous estimate or alpha_init) and the mask of stage i
   auto fetch = [&](int i, float& a_out, int& m_out) {
@@ -238,15 +243,21 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     const bool valid = inb && fin && m_cur == 0;
     const float pp = pe + (rho - 1.f) * muv - coff;
     const float r = albedo ? rho : 1.f;
-    float al;
+    float al, a_en, pen = 0.f;
     if (!iter) {
       const float a0 = p.alpha_init ? a_cur : (r > 0.f ? pp / (r * q) : 0.f);
       al = line.n_iter == 0 ? a0 : fmaxf(a0, 0.f);
+      a_en = a0;  // the initial iterate is the unclamped estimate
     } else {
       const float w = sparse ? 1.f / (a_cur + eps) : 0.f;
-      float pen = lam * w;
+      pen = lam * w;
       if (pna) pen = r > 0.f ? pen / r : 0.f;
       al = r > 0.f ? fmaxf((pp - pen) / (r * q), 0.f) : 0.f;
+      a_en = al;
+    }
+    if (want_energy && e == 0 && valid && !failed && r > 0.f) {
+      const float ra = r * a_en;
+      en += ra * (fmaf(ra, q, -2.f * pp) + 2.f * pen);
     }
     if (!valid)
       al = 0.f;
@@ -280,11 +291,11 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     }
     return;
   }
-  if (!accumulate) return;
+  if (!accumulate && !want_energy) return;
 
   // ---- moments of the tile, per column: sum over the 8 warps (fixed
   // order); every copy has landed and been read, so the stages are free
-  const int E3 = B + 3;
+  const int E3 = k3_entries(B);
   float* red = reinterpret_cast<float*>(smem_raw);  // [kStageRows][kTileCols][E3]
   float* mine = red + ((size_t)warp * kTileCols + s_col) * E3;
 #pragma unroll
@@ -301,9 +312,10 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     mine[0] = sb;
     mine[1] = sb2;
     mine[2] = sba;
+    mine[B + 3] = en;
   }
   __syncthreads();
-  const int K3E = k3_entries(B);
+  const int K3E = E3;
   for (int t = tid; t < nc * E3; t += kPixThreads) {
     const int cc = t / E3, j = t % E3;
     float sum = 0.f;

@@ -196,6 +196,9 @@ __device__ void fail_partition(const Params& p, int part, bool init) {
     p.status[part] = MF_ERR_NOT_SPD;
     reinterpret_cast<float4*>(p.pscal)[part] = make_float4(1.f, 0.f, 0.f, 0.f);
   }
+  if (p.energy)
+    for (int k = threadIdx.x; k < p.energy_stride; k += kThreads)
+      p.energy[(size_t)part * p.energy_stride + k] = __longlong_as_double(0x7ff8000000000000LL);
 }
 
 }  // namespace
@@ -300,6 +303,9 @@ __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
                     1.0f / df_to_float(n2));
     double* ds = p.dscal + (size_t)part * 4;
     ds[DS_N] = df_to_double(N);
+    // objective at the initial iterate: sum_i (x_i - mu^0)^T (C^0)^-1 (x_i - mu^0)
+    // = N tr((C^0)^-1 C^0) = N B; the pixel pass adds its per-pixel terms
+    if (p.energy) p.energy[(size_t)part * p.energy_stride] = df_to_double(N) * (double)B;
     ds[DS_BBAR] = 0.0;
     ds[DS_Q] = df_to_double(q);
     ds[DS_N2] = df_to_double(n2);
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
   const LineInfo& line = p.lines[part_line(p, part)];
   const int nunits = part_ncols(p, part) * line.n_rb;
   const float* P0 = p.k3part + (size_t)(line.k3u0 + (long long)part_col0(p, part) * line.n_rb) * K3E;
-  for (int t = tid; t < B + 3; t += kThreads) {
+  for (int t = tid; t < B + 4; t += kThreads) {
     df s{0.f, 0.f};
     for (int u = 0; u < nunits; ++u) s = df_addf(s, P0[(size_t)u * K3E + t]);
     mom[t] = s;
@@ -485,6 +491,32 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
       }
       hr = fabsf(det.hi) / fmaxf(hr, 1e-30f);
       s_bad = (!(det.hi > 0.f) || !df_isfinite(det)) ? 1 : (hr < 1e-8f ? 2 : 0);
+      if (p.energy) {
+        // objective at this iterate (Eq. (8) with the shrinkage step's
+        // per-pixel form): sum_i (x_i - mu^k)^T (C^k)^-1 (x_i - mu^k)
+        //   = N tr((C^k)^-1 S^k),  S^k = C^0 + (mu^0 - mu^k)(mu^0 - mu^k)^T,
+        // mu^0 - mu^k = mean(beta) t^{k-1} = mean(beta) U e, e = (0, 1, 1);
+        // with G = U^T (C^k)^-1 U = W (I + M W)^-1 (Woodbury) this is
+        //   N (B - tr(G M) + mean(beta)^2 e^T G e)
+        df G[9];
+        const df idet = df_recip(det);
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            df g = zero;
+            for (int k = 0; k < 3; ++k) g = df_fma(s_W[i * 3 + k], cf[j * 3 + k], g);
+            G[i * 3 + j] = df_mul(g, idet);
+          }
+        df trGM = zero;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) trGM = df_fma(G[i * 3 + j], Mrow(j, i), trGM);
+        const df eGe = df_add(df_add(G[4], G[5]), df_add(G[7], G[8]));
+        const df per = df_add(df_sub(df{(float)B, 0.f}, trGM), df_mul(mb2, eGe));
+        const double* dsn = p.dscal + (size_t)part * 4;
+        double* en = p.energy + (size_t)part * p.energy_stride;
+        en[pass] = s_bad == 0 ? dsn[DS_N] * df_to_double(per)
+                              : __longlong_as_double(0x7ff8000000000000LL);
+        en[pass - 1] += df_to_double(mom[B + 3]);  // the previous pass's pixel terms
+      }
     }
   }
   __syncthreads();
@@ -671,6 +703,27 @@ cudaError_t solve_set_attributes(size_t s_init, size_t s_iter, size_t s_lit) {
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(solve_literal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)s_lit);
+}
+
+// After the last pixel pass k: add its per-pixel objective terms (moment
+// slot B + 3 of the pass's per-CTA partials) to the energy of iterate k.
+// One warp per partition, fixed order.
+__global__ void energy_final_kernel(Params p, int k) {
+  const int part = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (part >= p.P || p.status[part] != MF_OK) return;
+  const int K3E = k3_entries(p.B);
+  const LineInfo& line = p.lines[part_line(p, part)];
+  const int nunits = part_ncols(p, part) * line.n_rb;
+  const float* P0 = p.k3part + (size_t)(line.k3u0 + (long long)part_col0(p, part) * line.n_rb) * K3E;
+  df s{0.f, 0.f};
+  for (int u = lane; u < nunits; u += 32) s = df_addf(s, P0[(size_t)u * K3E + p.B + 3]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o));
+  if (lane == 0) p.energy[(size_t)part * p.energy_stride + k] += df_to_double(s);
+}
+void energy_final_launch(cudaStream_t s, const Params& p, int k) {
+  energy_final_kernel<<<(p.P + 3) / 4, 128, 0, s>>>(p, k);
 }
 
 void solve_init_launch(size_t smem, cudaStream_t s, const Params& p) {

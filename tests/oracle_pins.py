@@ -364,7 +364,55 @@ def pin_plume_recovery(impl, scene):
     assert (a0 < 0).any() and (a >= 0).all()
 
 
+# ------------------------------------------ energy of the iterates (Fig. 5)
+def pin_energy_initial(impl):
+    """Iterate 0 has no penalty and r_i a = p_i / q, so each term of Eq. (8)
+    is (x_i - mu)^T C^-1 (x_i - mu) - p_i^2 / q; with C the sample covariance
+    about mu the first part sums to N tr(C^-1 C) = N B.  Closed form with the
+    sample mean, np.cov and a general solve, with and without the albedo
+    factor (it cancels)."""
+    for seed, flags in ((20, ALBEDO | SPARSE), (21, SPARSE), (22, ALBEDO)):
+        X, k, _ = tiny_partition(seed=seed, N=50, B=5)
+        N, B = X.shape
+        mu = X.mean(axis=0)
+        C = np.cov(X.T, bias=True)
+        t = mu * k
+        v = np.linalg.solve(C, t)
+        p = (X - mu) @ v
+        want = N * B - np.sum(p * p) / (t @ v)
+        for n in (0, 2):
+            E = impl.partition_energy(X, k, lam=0.1, eps=1e-3, n_iter=n, flags=flags)
+            assert E.shape == (n + 1,)
+            np.testing.assert_allclose(E[0], want, rtol=1e-10)
+
+
+def pin_energy_objective(impl):
+    """Every later iterate's energy is the sum over pixels of the objective of
+    Eq. (8) (``_paper_objective``, coded here) at that iterate's state, and no
+    larger than at a = 0 (each alpha_i^k minimises its term over a >= 0)."""
+    for (lam, flags) in ((1e-3, ALBEDO | SPARSE), (0.5, ALBEDO | SPARSE | PENALTY_NO_ALBEDO),
+                         (1e-2, SPARSE)):
+        X, k, _ = tiny_partition(seed=30, N=48, B=5)
+        eps = 1e-2
+        E = impl.partition_energy(X, k, lam=lam, eps=eps, n_iter=3, flags=flags)
+        _, tr = impl.retrieve_partition(X, k, lam=lam, eps=eps, n_iter=3, flags=flags, trace=True)
+        r = tr["r"]
+        prev = np.maximum(tr["alpha"][0], 0.0)
+        for it in range(1, 4):
+            mu, C, t = tr["mu"][it], tr["C"][it], tr["t"][it]
+            pen = lam / (prev + eps) / (r if flags & PENALTY_NO_ALBEDO else 1.0)
+            a = tr["alpha"][it]
+            terms = [_paper_objective(np.array([a[i]]), X[i] - mu, r[i], C, t, pen[i])[0]
+                     for i in range(len(X))]
+            zero = [_paper_objective(np.array([0.0]), X[i] - mu, r[i], C, t, pen[i])[0]
+                    for i in range(len(X))]
+            np.testing.assert_allclose(E[it], np.sum(terms), rtol=1e-10)
+            assert E[it] <= np.sum(zero) * (1 + 1e-12)
+            prev = a
+
+
 PINS = [pin_closed_form, pin_single_iteration, pin_nonnegative, pin_brute_force, pin_kkt,
         pin_scale_invariance, pin_band_permutation, pin_row_permutation, pin_duplication,
         pin_lambda_zero_scale, pin_mask_isolation, pin_partition_independence,
-        pin_sticky_zero, pin_single_band, pin_constant_absorption, pin_single_band_absorption]
+        pin_sticky_zero, pin_single_band, pin_constant_absorption, pin_single_band_absorption,
+        pin_energy_initial, pin_energy_objective]

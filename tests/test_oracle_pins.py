@@ -80,6 +80,12 @@ MUTATIONS = {
     "target_wrong_mean": ("t_new = target_spectrum(mu_new, s)", "t_new = target_spectrum(mu, s)"),
     "no_albedo_pen_ignored": ("if no_albedo_pen:", "if False:"),
     "mask_ignored": ("ok &= (np.asarray(mask) == 0)", "ok &= True"),
+    "energy_penalty_halved": ("E[k] = float(np.sum(D.T * Z) + 2.0 * np.sum(tr[\"pen\"][k] * ra))",
+                              "E[k] = float(np.sum(D.T * Z) + np.sum(tr[\"pen\"][k] * ra))"),
+    "energy_initial_clamped": ("        a = tr[\"alpha\"][k]\n        ra = np.where(r > 0, r * a, 0.0)",
+                               "        a = np.maximum(tr[\"alpha\"][k], 0.0)\n        ra = np.where(r > 0, r * a, 0.0)"),
+    "energy_without_albedo_in_residual": ("        ra = np.where(r > 0, r * a, 0.0)\n        D = (X",
+                                          "        ra = np.where(r > 0, a, 0.0)\n        D = (X"),
 }
 
 
