@@ -134,8 +134,12 @@ __global__ void __launch_bounds__(kThreads) bwd_pre_kernel(Params p, BwdParams b
 }
 
 // ------------------------------------------------------------ pixel passes
+// two CTAs per SM (16 warps to hide the per-pixel latency) while the
+// register cap that implies costs few spills (NJ <= 9); one above
+constexpr int bw_ctas_per_sm(int nj) { return nj <= 9 ? 2 : 1; }
+
 template <int NJ>
-__global__ void __launch_bounds__(kBwThreads, 1)
+__global__ void __launch_bounds__(kBwThreads, bw_ctas_per_sm(NJ))
     bwd_pixel_kernel(const __grid_constant__ CUtensorMap map, Params p, BwdParams b, int k,
                      int phase) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
