@@ -85,7 +85,13 @@ typedef struct {
  * sums, counters, status).  Supported: 8 <= B <= 128, B % 4 == 0,
  * band_lo % 4 == 0, bands_total % 4 == 0 (16-byte aligned pixel windows),
  * rows * col_group > B.  Uses the current CUDA device.  *out is owned by the
- * caller and released with mf_destroy. */
+ * caller and released with mf_destroy.
+ * Environment read here (all optional): MF_GRAPH=0 launches the kernels
+ * directly instead of replaying a CUDA graph; MF_RB_ROWS / MF_SC_ROWS set the
+ * rows per pixel-kernel CTA / per statistics item (as mf_tuning);
+ * MF_FORCE_DIRECT=1 (a test hook) sends every fused iteration's solve through
+ * the direct factorisation of C^k that otherwise serves only ill-conditioned
+ * Woodbury systems. */
 mf_status mf_plan(const mf_desc* desc, mf_plan_t* out);
 
 /* Release a plan and its device memory (synchronises the device first). */

@@ -331,6 +331,8 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   // 1024 rows in the tensor-core form (float32 sums in tensor memory) and
   // 2048 otherwise.  Every line is split evenly into whole blocks / chunks.
   p.n_ct = (p.cols + mf::kTileCols - 1) / mf::kTileCols;
+  // test hook: every fused iteration through the direct factorisation
+  p.force_direct = env_int("MF_FORCE_DIRECT", 0) != 0;
   {
     // the share of the cube that a pixel pass leaves in L2 for the next one:
     // about 3/4 of the L2 (the rest holds the pass's writes and moments)

@@ -71,6 +71,8 @@ struct Params {
   float eps;
   float l2_keep;          // pixel passes: fraction of each CTA's stages read last that
                           // are kept in L2 for the next pass (it walks the rows back)
+  int force_direct;       // test hook (MF_FORCE_DIRECT=1 at plan creation): every fused
+                          // iteration takes the direct factorisation of C^k
   double* energy;         // optional: (P, energy_stride) objective per iterate (null = off)
   int energy_stride;      // n_iter + 1
   const LineInfo* lines;  // device, n_lines

@@ -491,6 +491,7 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
       }
       hr = fabsf(det.hi) / fmaxf(hr, 1e-30f);
       s_bad = (!(det.hi > 0.f) || !df_isfinite(det)) ? 1 : (hr < 1e-8f ? 2 : 0);
+      if (s_bad == 0 && p.force_direct) s_bad = 2;
       if (p.energy) {
         // objective at this iterate (Eq. (8) with the shrinkage step's
         // per-pixel form): sum_i (x_i - mu^k)^T (C^k)^-1 (x_i - mu^k)

@@ -308,6 +308,18 @@ def test_bf16split_background_every_partition(rows, cols, bands):
 
 
 @pytest.mark.parametrize("precision", [0, BF16SPLIT])
+def test_direct_solve_path(monkeypatch, precision):
+    """Every fused iteration through the direct factorisation of C^k = C^0 +
+    U M U^T (the path ill-conditioned Woodbury systems take): the same
+    retrieval within the same bar."""
+    monkeypatch.setenv("MF_FORCE_DIRECT", "1")
+    sc = make_scene(700, 12, 72, n_plumes=3, plume_sigma=(3.0, 6.0),
+                    plume_peak=(1000.0, 5000.0), mask_frac=0.03, seed=23)
+    compare(sc.cube.numpy(), sc.k, 1e-3, 1e-9, 8, mask=sc.mask.numpy(), precision=precision,
+            tol=TOL_BF16SPLIT if precision else TOL_FP32)
+
+
+@pytest.mark.parametrize("precision", [0, BF16SPLIT])
 def test_exp_forward_model(precision):
     """A scene drawn with the unlinearised Beer-Lambert law (Sec. II-A): the
     filter's model is the first-order expansion, but the retrieval is still
