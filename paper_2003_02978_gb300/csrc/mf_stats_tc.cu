@@ -394,26 +394,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // this lane's byte offset of group f = e + 2 j in an operand set:
     // K group, row within the core matrix, n0 = 4 f -> j * 128 + 8 e
     const size_t kbase = (size_t)(slot >> 3) * L.kstride + (size_t)(slot & 7) * 16 + 8 * e;
-    // mask (and alpha) of the pixel of stage s of item `it`, prefetched one
-    // stage ahead
-    auto fetch = [&](const StatItem& it, int s, int& m_out, float& a_out) {
+    // mask (and alpha) of this lane's pixel, prefetched two stages ahead
+    // along the CTA's sequence of (item, stage): a cursor (pw, ps) walks that
+    // sequence and a two-deep queue holds what it loaded
+    int pw = blockIdx.x, ps = 0, pnst = 0;
+    StatItem pit{};
+    auto seek = [&]() {  // the first item from pw on with stages
+      for (; pw < nitems; pw += gridDim.x) {
+        item_geom(pw, pit, pnst);
+        if (pnst > 0) return;
+      }
+    };
+    auto fetch = [&](int& m_out, float& a_out) {
       m_out = 0;
       a_out = 0.f;
-      const int row = it.r_beg + s * kTcRows + slot;
-      if (row < it.r_end) {
-        const size_t pix = (size_t)row * p.cols + it.c;
+      if (pw >= nitems) return;
+      const int row = pit.r_beg + ps * kTcRows + slot;
+      if (row < pit.r_end) {
+        const size_t pix = (size_t)row * p.cols + pit.c;
         if (p.mask) m_out = p.mask[pix];
         if (mode == STAT_LITERAL) a_out = p.alpha[pix];
       }
+      if (++ps >= pnst) {
+        ps = 0;
+        pw += gridDim.x;
+        seek();
+      }
     };
-    int m_nx = 0;
-    float a_nx = 0.f;
-    if (blockIdx.x < nitems) {
-      StatItem it0;
-      int nst0;
-      item_geom(blockIdx.x, it0, nst0);
-      if (nst0 > 0) fetch(it0, 0, m_nx, a_nx);
-    }
+    seek();
+    int m_q0, m_q1;
+    float a_q0, a_q1;
+    fetch(m_q0, a_q0);
+    fetch(m_q1, a_q1);
     int g = 0, t = 0;
     // reference direction of an item's partition, double-buffered by item:
     // the next item's is loaded into registers during the current item and
@@ -451,18 +463,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int f = e + 2 * j;
         rf[j] = f < B4 ? reinterpret_cast<const float4*>(ref)[f] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      // the item after this one, for the prefetch at its last stage
-      StatItem it_nx;
-      int nst_nx = 0;
-      if (w + (int)gridDim.x < nitems) item_geom(w + gridDim.x, it_nx, nst_nx);
       for (int s = 0; s < nst; ++s, ++g) {
-        const int m_cur = m_nx;
-        const float a_cur = a_nx;
-        if (s + 1 < nst) {
-          fetch(it, s + 1, m_nx, a_nx);
-        } else if (nst_nx > 0) {
-          fetch(it_nx, 0, m_nx, a_nx);
-        }
+        const int m_cur = m_q0;
+        const float a_cur = a_q0;
+        m_q0 = m_q1;
+        a_q0 = a_q1;
+        fetch(m_q1, a_q1);
         if (__any_sync(0xffffffffu, failed || *(volatile int*)&s_abort)) {
           failed = true;
           continue;
