@@ -226,13 +226,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tmem_alloc(tslot, kTmemCols);
     tmem_relinquish();
   }
-  // the zero columns of both operand sets (never written again)
-  for (int i = tid; i < 2 * (kTcRows / 8) * (int)(L.pad_bytes / 16); i += kTcThreads) {
-    const int per = (int)(L.pad_bytes / 16);
-    const int kg = i / per, r = i - kg * per;  // K group (over both sets), 16-byte word
-    *reinterpret_cast<uint4*>(ops + (size_t)kg * L.kstride + L.pad_off + (size_t)r * 16) =
-        make_uint4(0u, 0u, 0u, 0u);
-  }
+  // both operand sets zeroed: the pad columns after L and the groups of
+  // H and L past the last band group and the augmentation are never
+  // written again
+  for (size_t i = tid; i < 2 * L.opb / 16; i += kTcThreads)
+    reinterpret_cast<uint4*>(ops)[i] = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -513,19 +511,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           aug = make_float4(rho - 1.f, bcf, 1.f, 0.f);
         }
-        // groups f = e + 2 j of the augmented vector [e, rho - 1, bcf, 1, 0 ..]
-        // up to NP: bands, the augmentation at f = B4, zeros after it
+        // an excluded pixel contributes nothing (rare: a warp-uniform branch)
+        if (__any_sync(0xffffffffu, !valid) && !valid) {
 #pragma unroll
-        for (int j = 0; j < NJ + 2; ++j) {
-          const int f = e + 2 * j;
-          if (4 * f >= NP) break;
-          float4 v;
-          if (j < NJ && f < B4) v = valid ? x[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-          else v = f == B4 ? aug : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int j = 0; j < NJ; ++j) x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // groups f = e + 2 j of the augmented vector [e, rho - 1, bcf, 1, 0 ..]:
+        // the augmentation at f = B4, then the bands (x[j] is zero past B4
+        // for a valid pixel, since the reference is) except the group the
+        // augmentation took (the same lane's).  Groups that no stage writes
+        // were zeroed at kernel start.
+        const int j_aug = e == (B4 & 1) ? (B4 >> 1) : -1;
+        {
           uint2 hi, lo;
-          split_bf16x4(v, hi, lo);
-          *reinterpret_cast<uint2*>(H + (size_t)j * 128) = hi;
-          *reinterpret_cast<uint2*>(Lo + (size_t)j * 128) = lo;
+          split_bf16x4(aug, hi, lo);
+          if (j_aug >= 0) {
+            *reinterpret_cast<uint2*>(H + (size_t)j_aug * 128) = hi;
+            *reinterpret_cast<uint2*>(Lo + (size_t)j_aug * 128) = lo;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          uint2 hi, lo;
+          split_bf16x4(x[j], hi, lo);
+          if (j != j_aug && 4 * (e + 2 * j) < NP) {
+            *reinterpret_cast<uint2*>(H + (size_t)j * 128) = hi;
+            *reinterpret_cast<uint2*>(Lo + (size_t)j * 128) = lo;
+          }
         }
         fence_proxy_async_smem();  // operand writes -> tensor core (async proxy)
         __syncwarp();
