@@ -251,14 +251,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---------------- producer
     if (lane == 0) {
       prefetch_tmap(&map);
-      int g = 0;
+      int fb = 0;         // float32 stage of the g-th copy: g % NF
+      uint32_t fph = 0;   // its phase parity: (g / NF) & 1
       for (int w = blockIdx.x; w < nitems && !failed; w += gridDim.x) {
         StatItem it;
         int nst;
         item_geom(w, it, nst);
-        for (int s = 0; s < nst; ++s, ++g) {
-          const int fb = g % NF;
-          if (!mbar_wait(&fp_empty[fb], (uint32_t)(((g / NF) & 1) ^ 1))) {
+        for (int s = 0; s < nst; ++s, (++fb == NF ? (fb = 0, fph ^= 1u) : 0u)) {
+          if (!mbar_wait(&fp_empty[fb], fph ^ 1u)) {
             failed = true;
             atomicExch(&s_abort, 1);
             break;
@@ -341,7 +341,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t acc = tmem + lanes + (uint32_t)(sb * L.accw);
         const bool last = s == nst - 1;
         // batches of 32 columns (16-column loads of H^T H + L^T L, H^T L
-        // and the running sum, one wait per batch)
+        // and the running sum, one wait per batch); a warp whose rows of D
+        // all lie past the augmented width (rows 96 .. 127) has nothing to
+        // add or store
         for (int c0 = 0; c0 < NP; c0 += 32) {
           const bool two = c0 + 16 < NP;
           uint32_t hh[32], hl[32], qs[32];
@@ -425,6 +427,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     fetch(m_q0, a_q0);
     fetch(m_q1, a_q1);
     int g = 0, t = 0;
+    int fb = 0;         // float32 stage of the g-th stage: g % NF
+    uint32_t fph = 0;   // its phase parity: (g / NF) & 1
     // reference direction of an item's partition, double-buffered by item:
     // the next item's is loaded into registers during the current item and
     // published by the named barrier that ends it
@@ -461,7 +465,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int f = e + 2 * j;
         rf[j] = f < B4 ? reinterpret_cast<const float4*>(ref)[f] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      for (int s = 0; s < nst; ++s, ++g) {
+      for (int s = 0; s < nst; ++s, ++g, (++fb == NF ? (fb = 0, fph ^= 1u) : 0u)) {
         const int m_cur = m_q0;
         const float a_cur = a_q0;
         m_q0 = m_q1;
@@ -471,11 +475,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           failed = true;
           continue;
         }
-        const int fb = g % NF, sb = g & 1;
+        const int sb = g & 1;
         const int row = it.r_beg + s * kTcRows + slot;
         const bool inb = row < it.r_end;
         // warp-uniform decision: the shuffles below need every lane
-        const bool ok_w = mbar_wait(&fp_full[fb], (uint32_t)((g / NF) & 1)) &&
+        const bool ok_w = mbar_wait(&fp_full[fb], fph) &&
                           mbar_wait(&op_empty[sb], (uint32_t)(((g >> 1) & 1) ^ 1));
         if (!__all_sync(0xffffffffu, ok_w)) {
           failed = true;
