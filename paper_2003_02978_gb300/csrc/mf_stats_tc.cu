@@ -23,18 +23,19 @@
 // stored as the pair (Q_ab, Q_ba), read as their sum).
 //
 // Persistent, warp-specialised kernel: one CTA per SM walks work items
-// (detector column, chunk of at most 1024 rows) with hand-offs on
-// shared-memory mbarriers only:
-//   warp 8 (producer): TMA box of 128 rows x B bands (float32) -> one of two
-//            float32 stages
+// (detector column, chunk of at most 1024 rows) of 128-pixel stages, with
+// hand-offs on shared-memory mbarriers only:
+//   warp 8 (producer): TMA box of 128 rows x B bands (float32) -> one of
+//            three float32 stages (two for the widest windows)
 //   warps 0-7 (converters, a lane pair per pixel): albedo split,
 //            augmentation, bf16 hi/lo into MN-major core matrices of one of
 //            two operand sets
 //   warp 9 (issuer, one lane): 8 x 2 MMAs (K = 16 pixels each) per stage into
-//            one of two tensor-memory accumulators (alternating per item);
-//            tcgen05.commit frees the operand set / publishes the item
-//   warps 10-13 (epilogue): tcgen05.ld of a finished accumulator, moments of
-//            the item written as float pairs, accumulator released.
+//            one of two tensor-memory accumulators (alternating per stage);
+//            tcgen05.commit frees the operand set and publishes the stage
+//   warps 10-13 (epilogue): tcgen05.ld of a finished stage accumulator, added
+//            into the item's running sum in tensor memory; after the item's
+//            last stage its moments are written as float pairs.
 // The reference direction of each partition (the mean of its first few
 // valid pixels, or mu^0) comes from global memory (pilot_kernel below for
 // the initialisation).
