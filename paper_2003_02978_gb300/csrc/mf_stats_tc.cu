@@ -342,9 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t acc = tmem + lanes + (uint32_t)(sb * L.accw);
         const bool last = s == nst - 1;
         // batches of 32 columns (16-column loads of H^T H + L^T L, H^T L
-        // and the running sum, one wait per batch); a warp whose rows of D
-        // all lie past the augmented width (rows 96 .. 127) has nothing to
-        // add or store
+        // and the running sum, one wait per batch)
         for (int c0 = 0; c0 < NP; c0 += 32) {
           const bool two = c0 + 16 < NP;
           uint32_t hh[32], hl[32], qs[32];
