@@ -351,9 +351,14 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   hp = std::max(hp, mf::kStageRows);
   int hs = tune && tune->stat_rows > 0 ? tune->stat_rows : env_int("MF_SC_ROWS", 0);
   if (hs <= 0) {
-    const long target_ctas = 2400;
-    const long nsc = std::max<long>(1, (target_ctas + p.cols - 1) / p.cols);
-    hs = (int)std::min<long>(d->precision == MF_BF16SPLIT ? 1024 : 2048, (p.rows + nsc - 1) / nsc);
+    // the float32 statistics kernel runs one CTA per item and wants many;
+    // the tensor-core one is persistent (one CTA per SM walking the items),
+    // balanced with about eight items per SM, and longer items (up to 1024
+    // rows) mean fewer per-item epilogues and moment partials
+    const bool tc = d->precision == MF_BF16SPLIT;
+    const long target_items = tc ? 8L * pl->num_sms : 2400;
+    const long nsc = std::max<long>(1, (target_items + p.cols - 1) / p.cols);
+    hs = (int)std::min<long>(tc ? 1024 : 2048, (p.rows + nsc - 1) / nsc);
   }
   hs = std::max(hs, mf::kStatRows);
   auto round_up = [](int x, int m) { return (x + m - 1) / m * m; };
