@@ -202,7 +202,10 @@ def run_reference(args, world, rank):
     sc, prm = workload_scene(WORKLOAD, seed=0, device="cpu")
     rows = sc.cube.shape[0]
     rng = np.random.default_rng(123)
-    ncol = 6
+    # whole partitions per step: 6 (about half a second of oracle work on
+    # 8-16 cores), fewer for long runs so that warm-up + K steps stay within
+    # a couple of minutes
+    ncol = max(1, min(6, 1200 // max(1, args.steps + args.warmup)))
     times = []
     for step in range(args.warmup + args.steps):
         cols = np.sort(rng.choice(sc.cube.shape[1], size=ncol, replace=False))
