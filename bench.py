@@ -237,8 +237,9 @@ def batched_form(args, dev, precision):
     U(0, 0.3), per-line n_iter in 5..20 and lambda log-uniform in
     [1e-4, 1e-2]; one shared target spectrum), stacked along rows: Mpixel/s of
     one batched retrieval (CUDA-graph replay) against the plain FP32 form
-    (literal schedule, one single-line plan per line, in sequence), with the
-    alpha error of both against the FP64 oracle on sampled partitions."""
+    (literal schedule, one single-line plan per line, in sequence).  The
+    oracle runs only in the CPU-baseline leg of this script; the batched
+    form's parity with it is tested per line in tests/test_batched.py."""
     import torch
     import paper_2003_02978_gb300 as mfg
     from synth import batched_lines, make_scene
@@ -285,29 +286,6 @@ def batched_form(args, dev, precision):
     ms_p = e0.elapsed_time(e1)
     for pl_ in plain:
         pl_.close()
-    err = None
-    if not args.no_oracle:
-        import oracle
-        err = {}
-        rng = np.random.default_rng(5)
-        for name, a in (("batched", out), ("plain_fp32", outp)):
-            num = den = mx = mref = 0.0
-            for li in (0, BATCH_LINES - 1):
-                cols = np.sort(rng.choice(598, 3, replace=False))
-                sub = cube[slices[li]][:, cols].cpu().numpy()
-                msk = mask[slices[li]][:, cols].cpu().numpy()
-                ref, _ = oracle.retrieve(sub.astype(np.float64),
-                                         np.asarray(k.cpu().numpy(), np.float64),
-                                         lams[li], 1e-9, nits[li], mask=msk)
-                valid = oracle.valid_pixels(sub, msk)
-                g = a[slices[li]][:, cols].cpu().numpy().astype(np.float64)
-                d = (g - ref)[valid]
-                num += float((d * d).sum())
-                den += float((ref[valid] ** 2).sum())
-                mx = max(mx, float(np.abs(d).max()))
-                mref = max(mref, float(np.abs(ref[valid]).max()))
-            err[name] = {"e_inf": mx / mref, "e_2": (num / den) ** 0.5,
-                         "sample": "3 random whole partitions of the first and last line"}
     del cube, mask, out, outp, scenes
     torch.cuda.empty_cache()
     return {"workload": f"{BATCH_LINES} flightlines, rows {rows}, 598 x 72, per-column masked "
@@ -315,7 +293,8 @@ def batched_form(args, dev, precision):
             "pixels": npix, "precision": "bf16split" if precision else "fp32",
             "value": npix / (ms_b * 1e-3) / 1e6, "ms_per_batch": ms_b,
             "plain_fp32_value": npix / (ms_p * 1e-3) / 1e6, "plain_fp32_ms": ms_p,
-            "status_ok": status_ok, "alpha_error": err}
+            "status_ok": status_ok,
+            "alpha_error": "per-line parity with the oracle is in the tests (test_batched.py)"}
 
 
 def differentiation_form(args, dev):
