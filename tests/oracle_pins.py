@@ -411,8 +411,66 @@ def pin_energy_objective(impl):
             prev = a
 
 
+# ---------------------------------------- amplification (the parity bound)
+def _fd_step(impl, X, k, lam, flags, a_start, i, n_iter=1):
+    """Central difference of alpha_i after n_iter steps started from a_start
+    with respect to the start value of pixel i."""
+    h = 1e-3 * a_start[i]
+    ap, am = a_start.copy(), a_start.copy()
+    ap[i] += h
+    am[i] -= h
+    run = lambda a: impl.retrieve_partition(X, k, lam=lam, n_iter=n_iter, flags=flags,
+                                            alpha_init=a)[i]
+    return (run(ap) - run(am)) / (2.0 * h)
+
+
+def pin_amplification(impl):
+    """The factor that widens the per-pixel parity bound is the derivative of
+    one shrinkage step with respect to the previous estimate (Eq. (5) inside
+    the step of Fig. 1, statistics held fixed), zero where the step clamps,
+    compounded over the steps as A^k = 1 + kappa^k A^{k-1} (a unit
+    perturbation entering at every step).  kappa is measured here by central
+    differences of the retrieval itself, started from a chosen estimate, on
+    background pixels: their own weight in the mean and covariance at
+    N = 2000 shifts the difference by at most ~0.015 from the fixed-statistics
+    derivative (~0.03 over two steps)."""
+    X, k, truth = tiny_partition(N=2000, B=6, seed=4, albedo_sigma=0.3)
+    a0 = np.abs(impl.retrieve_partition(X, k, n_iter=0)) + 10.0
+    bg = np.flatnonzero(truth == 0)
+    tol = lambda ref: 0.02 + 0.01 * abs(ref)
+    for lam, flags in ((0.5, ALBEDO | SPARSE), (1.0, ALBEDO | SPARSE | PENALTY_NO_ALBEDO)):
+        A1 = impl.amplification(X, k, lam=lam, n_iter=1, flags=flags, alpha_init=a0)
+        a1, tr = impl.retrieve_partition(X, k, lam=lam, n_iter=1, flags=flags, alpha_init=a0,
+                                         trace=True)
+        pos = [i for i in bg if a1[i] > 5.0][:6]
+        clamped = [i for i in bg if tr["pre"][1][i] < -5.0][:3]
+        assert len(pos) == 6 and len(clamped) == 3
+        for i in pos + clamped:
+            fd = _fd_step(impl, X, k, lam, flags, a0, i)
+            assert abs((A1[i] - 1.0) - fd) <= tol(fd), (i, A1[i] - 1.0, fd)
+        # two steps: with the compounding, kappa^2 = (A^2 - 1) / (1 + kappa^1),
+        # and the chain rule gives d alpha^2 / d alpha^0 = kappa^2 kappa^1
+        # (pixels with kappa^1 > 0.4, where the compounding is visible)
+        A2 = impl.amplification(X, k, lam=lam, n_iter=2, flags=flags, alpha_init=a0)
+        a2 = impl.retrieve_partition(X, k, lam=lam, n_iter=2, flags=flags, alpha_init=a0)
+        checked = 0
+        for i in bg:
+            if checked == 4:
+                break
+            if not (a1[i] > 5.0 and a2[i] > 5.0):
+                continue
+            k1 = _fd_step(impl, X, k, lam, flags, a0, i)
+            if k1 <= 0.4:
+                continue
+            fd2 = _fd_step(impl, X, k, lam, flags, a0, i, n_iter=2)
+            pred = (A2[i] - 1.0) / (1.0 + k1) * k1
+            assert abs(fd2 - pred) <= 0.03 + 0.02 * abs(fd2), (i, fd2, pred)
+            checked += 1
+        assert checked == 4
+
+
 PINS = [pin_closed_form, pin_single_iteration, pin_nonnegative, pin_brute_force, pin_kkt,
         pin_scale_invariance, pin_band_permutation, pin_row_permutation, pin_duplication,
         pin_lambda_zero_scale, pin_mask_isolation, pin_partition_independence,
         pin_sticky_zero, pin_single_band, pin_constant_absorption, pin_single_band_absorption,
-        pin_energy_initial, pin_energy_objective]
+        pin_energy_initial, pin_energy_objective, pin_amplification]

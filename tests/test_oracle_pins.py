@@ -86,6 +86,16 @@ MUTATIONS = {
                                "        a = np.maximum(tr[\"alpha\"][k], 0.0)\n        ra = np.where(r > 0, r * a, 0.0)"),
     "energy_without_albedo_in_residual": ("        ra = np.where(r > 0, r * a, 0.0)\n        D = (X",
                                           "        ra = np.where(r > 0, a, 0.0)\n        D = (X"),
+    # the amplification factor that widens the per-pixel parity bound
+    "amplification_w_not_squared": ("kap = lam * w * w / np.where(r > 0, r * q, np.inf)",
+                                    "kap = lam * w / np.where(r > 0, r * q, np.inf)"),
+    "amplification_without_r": ("kap = lam * w * w / np.where(r > 0, r * q, np.inf)",
+                                "kap = lam * w * w / np.where(r > 0, q, np.inf)"),
+    "amplification_clamp_ignored": ("kap = np.where(tr[\"alpha\"][k] > 0, kap, 0.0)", "kap = kap"),
+    "amplification_not_compounded": ("A = 1.0 + kap * A", "A = 1.0 + kap"),
+    "amplification_penalty_flag_ignored": (
+        "        if flags & PENALTY_NO_ALBEDO:\n            kap = kap /",
+        "        if False:\n            kap = kap /"),
 }
 
 
