@@ -6,7 +6,7 @@ and the CPU-baseline leg of ``bench.py``; never by the product path.
 from .mf_oracle import *  # noqa: F401,F403
 from .mf_oracle import (ALBEDO, SPARSE, LITERAL, PENALTY_NO_ALBEDO, NotSPD,  # noqa: F401
                         retrieve, retrieve_partition, partitions, matched_filter,
-                        pixel_energy, near_threshold, valid_pixels,
+                        pixel_energy, valid_pixels,
                         amplification, retrieve_amplification, partition_energy,
                         retrieve_energy)
 from .mf_grad import retrieve_partition_t, vjp as grad_vjp  # noqa: F401,E402

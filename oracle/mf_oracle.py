@@ -345,16 +345,3 @@ def retrieve_amplification(cube, s, lam=1.0, eps=1e-9, n_iter=10, mask=None, ban
             pass
         out[:, c0:c1] = blk
     return out
-
-
-def near_threshold(X, s, lam=1.0, eps=1e-9, n_iter=10, flags=ALBEDO | SPARSE, alpha_init=None,
-                   tol=1e-4):
-    """Pixels whose pre-clamp value (p - pen)/(r q) came within ``tol`` (in
-    alpha units) of the clamp at 0 at some step (the clamp of alpha^0 included),
-    so that a rounding difference may flip them across the threshold of
-    max(0, .) and, through w = 1/(alpha + eps), change their later history."""
-    _, tr = retrieve_partition(X, s, lam, eps, n_iter, flags, alpha_init, trace=True)
-    flag = np.zeros(X.shape[0], dtype=bool)
-    for pre in tr["pre"][: (n_iter + 1 if n_iter > 0 else 0)]:
-        flag |= np.abs(pre) < tol
-    return flag
