@@ -17,8 +17,9 @@ Concentration from Imaging Spectrometer Data Using Sparsity Prior", IEEE TGRS
   enhancement, then for k = 1..N_iter the weights of Eq. (5), the mean update
   of Eq. (10), the covariance update of Eq. (11) and the non-negative
   shrinkage update (Eq. (6) with the albedo factor of Sec. II-C);
-* the six variants of Table I through the ALBEDO / SPARSE switches named in
-  the caption of Fig. 1 ("without sparsity w = 0, without albedo r = 1").
+* the six variants of Table I through the ALBEDO / SPARSE switches that the
+  caption of Fig. 1 describes: no sparsity sets the weights to zero, no albedo
+  correction sets every r_i to one.
 
 Every statistic is recomputed literally from its defining sum at every
 iteration; no rank-update identity, no blocking, no fusion.  Linear systems
