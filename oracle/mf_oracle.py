@@ -10,7 +10,7 @@ What it computes (Foote et al., "Fast and Accurate Retrieval of Methane
 Concentration from Imaging Spectrometer Data Using Sparsity Prior", IEEE TGRS
 2020):
 
-* the classic matched filter closed form, Eq. (3);
+* the classic matched filter closed form, Eq. (3), as the initial estimate;
 * the albedo factor r_i of Eq. (7) and the target t = mu (.) s of Eq. (9);
 * the procedure of Fig. 1 (Algorithm AlbedoReWeightL1Filter), step by step,
   in the paper's order: initial mean and covariance, albedo, initial
@@ -40,7 +40,8 @@ R3  alpha^0 is clamped at 0 before it feeds w^1, mu^1 and C^1 (Sec. III-D: the
     non-iterative rows of Table I have negative values).
 R4  The shrinkage step is used exactly as printed in Fig. 1:
     alpha = max(0, (p - pen) / (r q)).  The per-pixel objective it minimises
-    exactly is f(a) = d^T C^-1 d + 2 pen r a on a >= 0 (see ``pixel_energy``).
+    exactly is f(a) = d^T C^-1 d + 2 pen r a on a >= 0, with
+    d = (L_i - mu^k) - r a t(mu^k) (used by ``partition_energy``).
 R5  pen = lam * w_i by default (penalty r_i w_i |a| of Eq. (8) in the
     r-scaled form); flag PENALTY_NO_ALBEDO gives pen = lam * w_i / r_i.
 R6  lam is a dimensionless multiplier on the paper's weight; lam = 1 is the
@@ -115,22 +116,6 @@ def spd_solve(C: np.ndarray, b: np.ndarray) -> np.ndarray:
         raise NotSPD(str(e)) from None
     y = solve_triangular(L, b, lower=True)
     return solve_triangular(L.T, y, lower=False)
-
-
-def matched_filter(X: np.ndarray, mu: np.ndarray, C: np.ndarray, t: np.ndarray) -> np.ndarray:
-    """Classic matched filter, Eq. (3): (L_i - mu)^T C^-1 t / t^T C^-1 t."""
-    v = spd_solve(C, t)
-    return ((X - mu) @ v) / (t @ v)
-
-
-def pixel_energy(a, xk, r, C, t, pen):
-    """Per-pixel objective minimised by the shrinkage step of Fig. 1 (R4):
-    f(a) = d^T C^-1 d + 2 pen r a,  d = (L_i - mu^k) - r a t(mu^k).
-    ``xk`` = L_i - mu^k.  Vectorised over ``a``."""
-    a = np.asarray(a, dtype=np.float64)
-    Ci = np.linalg.inv(C)
-    d = xk[None, :] - r * a[:, None] * t[None, :]
-    return np.einsum("ij,jk,ik->i", d, Ci, d) + 2.0 * pen * r * a
 
 
 def retrieve_partition(X, s, lam=1.0, eps=1e-9, n_iter=10, flags=ALBEDO | SPARSE,
@@ -257,8 +242,8 @@ def retrieve(cube, s, lam=1.0, eps=1e-9, n_iter=10, mask=None, band_lo=0, band_h
 def partition_energy(X, s, lam=1.0, eps=1e-9, n_iter=10, flags=ALBEDO | SPARSE):
     """Objective of every iterate of Fig. 1 on one partition (the energy of
     Fig. 5, Sec. III-B): E^k = sum_i f_i(alpha_i^k), k = 0..n_iter, with the
-    per-pixel objective f of R4 at iterate k's mu^k, C^k, t^k and pen^k
-    (``pixel_energy``), summed over the partition's pixels.  Iterate 0 is the
+    per-pixel objective f of R4 at iterate k's mu^k, C^k, t^k and pen^k,
+    summed over the partition's pixels.  Iterate 0 is the
     unclamped initial estimate with no penalty (R3: the clamp feeds the first
     reweighting, it is not part of the initial estimate).  Reading R17."""
     X = np.asarray(X, dtype=np.float64)

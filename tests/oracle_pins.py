@@ -469,8 +469,36 @@ def pin_amplification(impl):
         assert checked == 4
 
 
+# ------------------------------------------- the statistics primitives alone
+def pin_statistics_primitives(impl):
+    """The mean of Fig. 1, the covariance of Eq. (11) and the albedo factor of
+    Eq. (7) on inputs whose value is fixed by the definition: identical rows
+    have that row as mean and a zero covariance; the rows d and -d (N = 2)
+    have covariance d d^T, which has rank one and is not scaled by
+    N / (N - 1); for centred rows the 1/N covariance is numpy's biased
+    np.cov; the mean spectrum has albedo factor 1, c times it c, and a
+    spectrum orthogonal to it 0."""
+    rng = np.random.default_rng(11)
+    x = rng.uniform(1.0, 10.0, 7)
+    X = np.tile(x, (5, 1))
+    np.testing.assert_allclose(impl.mean_vector(X), x, rtol=1e-15)
+    np.testing.assert_allclose(impl.covariance_about(X - impl.mean_vector(X)), 0.0, atol=1e-24)
+    d = rng.normal(size=7)
+    np.testing.assert_allclose(impl.covariance_about(np.stack([d, -d])), np.outer(d, d),
+                               rtol=1e-14)
+    D = rng.normal(size=(50, 7))
+    D -= D.mean(axis=0)
+    np.testing.assert_allclose(impl.covariance_about(D), np.cov(D.T, bias=True), rtol=1e-12)
+    mu = rng.uniform(1.0, 10.0, 7)
+    o = rng.normal(size=7)
+    o -= (o @ mu) / (mu @ mu) * mu
+    r = impl.albedo_factor(np.stack([mu, 3.5 * mu, o]), mu)
+    np.testing.assert_allclose(r, [1.0, 3.5, 0.0], rtol=1e-14, atol=1e-14)
+
+
 PINS = [pin_closed_form, pin_single_iteration, pin_nonnegative, pin_brute_force, pin_kkt,
         pin_scale_invariance, pin_band_permutation, pin_row_permutation, pin_duplication,
         pin_lambda_zero_scale, pin_mask_isolation, pin_partition_independence,
         pin_sticky_zero, pin_single_band, pin_constant_absorption, pin_single_band_absorption,
-        pin_energy_initial, pin_energy_objective, pin_amplification]
+        pin_energy_initial, pin_energy_objective, pin_amplification,
+        pin_statistics_primitives]

@@ -1,10 +1,18 @@
 """Helpers shared by the GPU parity tests: oracle runs and the alpha metric."""
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 # FP32 path against the FP64 oracle: normwise relative error bound on alpha
 TOL_FP32 = 1e-4
+# ceiling on the amplification factor that may widen one pixel's bound: a
+# pixel amplified more than this is still checked, at this factor
+AMP_CAP = 1e3
+# at most this fraction of the valid pixels (rounded up) may use the widening,
+# i.e. miss the plain bound tol * max|ref|
+WIDEN_FRAC = 1e-4
 
 
 def alpha_errors(got, ref, valid):
@@ -23,22 +31,43 @@ def f32(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
-def check_alpha(got, ref, valid, amp, tol=TOL_FP32):
-    """The parity bar for float32 paths:
-    * e_2 (normwise relative, all valid pixels) <= tol;
-    * every pixel: |got - ref| <= tol * max|ref| * A_i, where A_i >= 1 is the
-      oracle's amplification factor of the reweighting map at that pixel
-      (``oracle.amplification``); A_i = 1 for all but a few pixels whose
-      previous estimate was tiny and positive, where any rounding is magnified
-      by lam w^2 / (r q) in every precision.
-    Returns (e_inf, e_2, e_inf_scaled, n_amplified)."""
+def alpha_report(got, ref, valid, amp, tol=TOL_FP32):
+    """Every figure of the parity bar (see ``check_alpha``) without asserting:
+    e_inf, e_2, e_sc (the error scaled by the capped amplification factor),
+    n_valid, n_amp (pixels with A_i > 10), max_amp, n_widened (pixels beyond
+    the plain bound tol * max|ref|) and n_widen_max (how many may be)."""
     g = np.asarray(got, dtype=np.float64)[valid]
     r = np.asarray(ref, dtype=np.float64)[valid]
     a = np.asarray(amp, dtype=np.float64)[valid]
     e_inf, e_2 = alpha_errors(got, ref, valid)
     scale = max(np.abs(r).max(), 1e-30) if r.size else 1.0
-    e_sc = float((np.abs(g - r) / (scale * a)).max()) if r.size else 0.0
-    n_amp = int((a > 10).sum())
-    assert e_2 <= tol, f"e_2 {e_2:.3e} > {tol} (e_inf {e_inf:.3e})"
-    assert e_sc <= tol, f"amplification-scaled e_inf {e_sc:.3e} > {tol} (raw e_inf {e_inf:.3e}, {n_amp} pixels with A > 10)"
-    return e_inf, e_2, e_sc, n_amp
+    d = np.abs(g - r)
+    e_sc = float((d / (scale * np.minimum(a, AMP_CAP))).max()) if r.size else 0.0
+    return {"e_inf": e_inf, "e_2": e_2, "e_sc": e_sc, "n_valid": int(r.size),
+            "n_amp": int((a > 10).sum()), "max_amp": float(a.max()) if r.size else 1.0,
+            "n_widened": int((d > tol * scale).sum()),
+            "n_widen_max": int(math.ceil(WIDEN_FRAC * r.size))}
+
+
+def check_alpha(got, ref, valid, amp, tol=TOL_FP32):
+    """The parity bar for float32 paths:
+    * e_2 (normwise relative, all valid pixels) <= tol;
+    * every pixel: |got - ref| <= tol * max|ref| * min(A_i, AMP_CAP), where
+      A_i >= 1 is the oracle's amplification factor of the reweighting map at
+      that pixel (``oracle.amplification``): the derivative of the shrinkage
+      step with respect to the previous estimate is lam w^2 / (r q), so where
+      the previous estimate was tiny and positive any rounding is magnified,
+      in every precision.  A_i is capped at AMP_CAP, so no pixel goes
+      unchecked;
+    * at most ceil(WIDEN_FRAC * n_valid) pixels may use that widening, i.e.
+      exceed the plain bound tol * max|ref|: an error spread over many
+      moderately amplified pixels fails.
+    Returns the dict of ``alpha_report``."""
+    rep = alpha_report(got, ref, valid, amp, tol)
+    info = (f"(e_inf {rep['e_inf']:.3e}, e_2 {rep['e_2']:.3e}, {rep['n_amp']} of "
+            f"{rep['n_valid']} pixels with A > 10, max A {rep['max_amp']:.3g}, "
+            f"{rep['n_widened']} beyond the plain bound, at most {rep['n_widen_max']})")
+    assert rep["e_2"] <= tol, f"e_2 {rep['e_2']:.3e} > {tol} {info}"
+    assert rep["e_sc"] <= tol, f"amplification-scaled e_inf {rep['e_sc']:.3e} > {tol} {info}"
+    assert rep["n_widened"] <= rep["n_widen_max"], f"too many widened pixels {info}"
+    return rep

@@ -72,6 +72,8 @@ MUTATIONS = {
                        "alpha = np.where(rpos, p / np.where(rpos, q, 1.0), 0.0)"),
     "albedo_uses_squared_norm_wrong": ("return (X @ mu) / (mu @ mu)",
                                        "return (X @ mu) / np.sqrt(mu @ mu)"),
+    "mean_wrong_normalisation": ("return X.sum(axis=0) / X.shape[0]",
+                                 "return X.sum(axis=0) / (X.shape[0] + 1)"),
     "cov_unbiased": ("return (D.T @ D) / D.shape[0]", "return (D.T @ D) / (D.shape[0] - 1)"),
     "cov_transposed_scalar": ("return (D.T @ D) / D.shape[0]",
                               "return np.diag(np.sum(D * D, axis=0)) / D.shape[0]"),
