@@ -91,7 +91,13 @@ typedef struct {
  * rows per pixel-kernel CTA / per statistics item (as mf_tuning);
  * MF_FORCE_DIRECT=1 (a test hook) sends every fused iteration's solve through
  * the direct factorisation of C^k that otherwise serves only ill-conditioned
- * Woodbury systems. */
+ * Woodbury systems.  MF_FAULT (a fault-injection hook for tests; nothing in
+ * it faults the GPU) forces a failure path: "alloc" makes mf_plan return
+ * MF_ERR_OOM before any CUDA call; "notspd" reports every partition's
+ * initial covariance as not positive definite (MF_ERR_NOT_SPD, alpha NaN);
+ * "timeout" makes every pixel-kernel CTA of the first pass wait 2000 cycles
+ * on a barrier nothing arrives on, so that it records MF_ERR_TIMEOUT (after
+ * its own copies have landed) and the later passes write NaN. */
 mf_status mf_plan(const mf_desc* desc, mf_plan_t* out);
 
 /* Release a plan and its device memory (synchronises the device first). */
@@ -250,10 +256,10 @@ mf_status mf_profile_read(mf_plan_t plan, double* ms, int64_t* launches, int32_t
 /* Initial background statistics of every partition -- the mean mu^0 and
  * covariance C^0 of Fig. 1's initialisation, as mf_background returns them
  * after a retrieval -- without allocating any device memory.  The paper has
- * no counterpart: this exists for callers that cannot allocate once running
- * (graph-replayed pipelines with a fixed memory plan, real-time processing
- * that forbids allocation after start-up, hosts whose device memory belongs
- * to another allocator), which therefore cannot create a plan.
+ * no counterpart: this exists for callers that may not allocate device memory
+ * once running (real-time processing that forbids allocation after start-up,
+ * hosts whose device memory belongs to another allocator that this library
+ * cannot call), which therefore cannot create a plan.
  *   desc   shape, band window and col_group (flags and precision unused)
  *   cube   device (rows, cols, bands_total) float32 BIP, 16-byte aligned
  *   mask   device (rows, cols) uint8, nonzero = excluded, or NULL
@@ -263,10 +269,13 @@ mf_status mf_profile_read(mf_plan_t plan, double* ms, int64_t* launches, int32_t
  * array that every GPU loading the library holds until exit; shapes whose
  * moments do not fit (P * col_group * 8 * K bytes, K = 16 * nb (nb + 1) / 2,
  * nb = (B + 4) / 4; about 24 KB per detector column at B = 72) return
- * MF_ERR_UNSUPPORTED.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) and sets kernel attributes: make it
- * before any stream capture.  Calls share the array: calls that overlap on
- * the GPU race.  Enqueued on `stream`, no synchronisation. */
+ * MF_ERR_UNSUPPORTED and enqueue nothing.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) and sets kernel
+ * attributes: make it before any stream capture; after a cudaDeviceReset the
+ * cached address is stale and the entry point must not be called again.
+ * Calls share the array (each rewrites its line table and clears its status
+ * words): calls that overlap on the GPU race.  Enqueued on `stream`, no
+ * synchronisation. */
 mf_status mf_background_noalloc(const mf_desc* desc, const float* cube, const uint8_t* mask,
                                 double* mu0, double* cov0, void* stream);
 

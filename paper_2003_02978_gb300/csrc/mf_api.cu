@@ -129,8 +129,8 @@ int nj_bucket(int B4) {
 cudaError_t set_attrs(const mf_plan_s* pl) {
   const int bmax_bucket = 8 * pl->nj;
   const int bmax = mf::kMaxB;
-  const int ba = (bmax + 3 + 3) / 4 * 4;
-  cudaError_t e = mf::stats_set_attributes(pl->nj, mf::stats_smem_bytes(bmax_bucket));
+  const int ba = mf::aug_width(bmax, mf::kMaxDirs);
+  cudaError_t e = mf::stats_set_attributes(pl->nj, mf::stats_smem_bytes(bmax_bucket, mf::kDirsFp32));
   if (e == cudaSuccess && pl->d.precision == MF_BF16SPLIT)
     e = mf::stats_tc_set_attributes(pl->nj, pl->smem_stats);
   if (e == cudaSuccess)
@@ -205,8 +205,10 @@ void stats_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int pass, cu
     if (mode == mf::STAT_INIT) mf::pilot_launch(s, prm);
     const int grid = std::min(pl->grid_stats, pl->num_sms);
     mf::stats_tc_launch(pl->nj, grid, pl->smem_stats, s, pl->map_stats, prm, mode, pass);
-  } else
+  } else {
+    if (mode == mf::STAT_INIT) mf::pilot_dirs_launch(s, prm);
     mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, pl->map_stats, prm, mode, pass);
+  }
   mark_end(m, s);
 }
 void pixel_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int acc, int pass,
@@ -296,6 +298,16 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   if (d->precision == MF_BF16SPLIT && !mf::stats_tc_supported(B))
     return fail(MF_ERR_UNSUPPORTED, "MF_BF16SPLIT supports windows of 64 to 92 bands, got %d", B);
 
+  // fault hook: MF_FAULT=alloc fails here as an exhausted device would,
+  // before any CUDA call; =notspd and =timeout are set in the plan below
+  const char* fault = std::getenv("MF_FAULT");
+  const std::string fault_s = fault ? fault : "";
+  if (fault_s == "alloc")
+    return fail(MF_ERR_OOM, "workspace allocation refused (fault hook MF_FAULT=alloc)");
+  if (!fault_s.empty() && fault_s != "notspd" && fault_s != "timeout")
+    return fail(MF_ERR_INVALID_ARG, "MF_FAULT=%s: expected alloc, notspd or timeout",
+                fault_s.c_str());
+
   mf_plan_s* pl = new mf_plan_s();
   pl->d = *d;
   pl->n_lines = n_lines;
@@ -309,7 +321,10 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   p.G = (int)std::min<int64_t>(d->col_group, d->cols);
   p.Pl = (p.cols + p.G - 1) / p.G;
   p.P = n_lines * p.Pl;
-  p.BA = (B + 3 + 3) / 4 * 4;
+  // reference directions of the statistics split: one for the tensor-core
+  // form, kDirsFp32 for the float32 statistics
+  p.K = d->precision == MF_BF16SPLIT ? 1 : mf::kDirsFp32;
+  p.BA = mf::aug_width(B, p.K);
   p.flags = d->flags;
   p.n_lines = n_lines;
   pl->nj = nj_bucket(p.B4);
@@ -333,6 +348,10 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   p.n_ct = (p.cols + mf::kTileCols - 1) / mf::kTileCols;
   // test hook: every fused iteration through the direct factorisation
   p.force_direct = env_int("MF_FORCE_DIRECT", 0) != 0;
+  // fault hooks: every initial factorisation reported not positive definite;
+  // every pixel CTA of pass 0 runs out of a 2000-cycle wait
+  p.fault_notspd = fault_s == "notspd";
+  p.test_wait = fault_s == "timeout" ? 2000 : 0;
   {
     // the share of the cube that a pixel pass leaves in L2 for the next one:
     // about 3/4 of the L2 (the rest holds the pass's writes and moments)
@@ -397,7 +416,7 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   pl->grid_stats = p.n_items;
   pl->grid_pixel = p.n_blocks;
   pl->smem_stats = d->precision == MF_BF16SPLIT ? mf::stats_tc_smem_bytes(B)
-                                                 : mf::stats_smem_bytes(B);
+                                                 : mf::stats_smem_bytes(B, p.K);
   pl->smem_pixel = mf::pixel_smem_bytes(B, pl->nj);
   pl->smem_sinit = mf::solve_init_smem_bytes(B, p.BA);
   pl->smem_siter = mf::solve_iter_smem_bytes(B);
@@ -413,7 +432,9 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   };
   Piece pieces[] = {
       {(void**)&lines_d, (size_t)n_lines * sizeof(mf::LineInfo)},
-      {(void**)&p.pilot, P * B * sizeof(float)},
+      {(void**)&p.pilot, P * p.K * B * sizeof(float)},
+      {(void**)&p.pilot_c, P * p.K * sizeof(float)},
+      {(void**)&p.pilot_s, P * p.K * sizeof(float)},
       {(void**)&p.mu0, P * B * sizeof(float2)},
       {(void**)&p.mu0f, P * B * sizeof(float)},
       {(void**)&p.vf, P * B * sizeof(float)},

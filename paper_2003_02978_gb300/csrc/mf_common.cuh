@@ -6,7 +6,9 @@
 //              [row0_l, row0_l + rows_l)), each line with its own partitions
 //   alpha      caller's (rows, cols) float32, updated in place every pass
 //   lines      (n_lines) LineInfo      per-line geometry, lambda and iteration count
-//   pilot      (P, B) float32        reference direction m of the initial statistics
+//   pilot      (P, K, B) float32     reference directions q_k of the statistics split
+//   pilot_c    (P, K) float32        their offsets c_k (coefficients of the pilot mean)
+//   pilot_s    (P, K) float32        their inverse squared norms 1 / (q_k . q_k)
 //   mu0        (P, B) double-float   initial mean mu^0
 //   mu0f       (P, B) float32        mu^0 rounded, as the pixel kernel holds it
 //   vf         (P, B) float32        v = C^{-1} t of the current pass
@@ -34,6 +36,14 @@ constexpr int kMaxB = 128;
 constexpr int kTileCols = 16;     // pixel kernel: adjacent columns per tile (one lane pair each)
 constexpr int kStageRows = 8;     // pixel kernel: rows per pipeline stage (one per consumer warp)
 constexpr int kStatRows = 128;    // statistics kernel: rows per pipeline stage
+// Reference directions of the statistics split: the float32 statistics use
+// kDirsFp32 (an orthonormal basis of the partition's first valid pixels),
+// the tensor-core form one (the mean of the first valid pixels)
+constexpr int kDirsFp32 = 8;
+constexpr int kMaxDirs = 8;
+// augmented width of the moments: B bands, K direction coefficients, the
+// target coefficient b and the constant 1, rounded up to a multiple of 4
+__host__ __device__ inline int aug_width(int B, int K) { return (B + K + 2 + 3) / 4 * 4; }
 
 enum : int { PS_Q = 0, PS_MUV, PS_COFF, PS_INVMU2, PS_N };
 enum : int { DS_N = 0, DS_BBAR, DS_Q, DS_N2 };
@@ -64,7 +74,8 @@ struct Params {
   // geometry
   int rows, cols, bands_total, band_lo, B, B4, G;
   int Pl, P;              // partitions per line, in all lines
-  int BA;                 // augmented width: roundup4(B + 3)
+  int K;                  // reference directions of the statistics split (1..kMaxDirs)
+  int BA;                 // augmented width: aug_width(B, K)
   int n_ct;               // pixel kernel column tiles
   int n_lines, n_items, n_blocks;  // lines; statistics items; pixel CTAs
   uint32_t flags;
@@ -73,6 +84,9 @@ struct Params {
                           // are kept in L2 for the next pass (it walks the rows back)
   int force_direct;       // test hook (MF_FORCE_DIRECT=1 at plan creation): every fused
                           // iteration takes the direct factorisation of C^k
+  long long test_wait;    // fault hook (MF_FAULT=timeout): > 0 makes every pixel CTA of
+                          // pass 0 wait this many cycles on a barrier nothing arrives on
+  int fault_notspd;       // fault hook (MF_FAULT=notspd): every initial factorisation fails
   double* energy;         // optional: (P, energy_stride) objective per iterate (null = off)
   int energy_stride;      // n_iter + 1
   const LineInfo* lines;  // device, n_lines
@@ -85,6 +99,8 @@ struct Params {
   float* albedo;
   // workspace
   float* pilot;
+  float* pilot_c;
+  float* pilot_s;
   float2* mu0;
   float* mu0f;
   float* vf;
@@ -217,7 +233,7 @@ __host__ __device__ inline void block_of(int t, int nb, int& bi, int& bj) {
 
 // ------------------------------------------------------- host-side launchers
 // (each defined in the translation unit that defines the kernel)
-size_t stats_smem_bytes(int B);
+size_t stats_smem_bytes(int B, int K);
 size_t pixel_smem_bytes(int B, int nj);
 int pixel_ctas_per_sm(int nj);  // resident pixel CTAs per SM for a template bucket
 size_t solve_init_smem_bytes(int B, int BA);
@@ -241,6 +257,7 @@ cudaError_t stats_tc_set_attributes(int nj, size_t smem);
 void stats_tc_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
                      const Params& p, int mode, int pass);
 void pilot_launch(cudaStream_t s, const Params& p);
+void pilot_dirs_launch(cudaStream_t s, const Params& p);
 void energy_final_launch(cudaStream_t s, const Params& p, int k);
 // backward pass (mf_backward.cu)
 size_t bwd_pixel_smem_bytes(int B, int nj);

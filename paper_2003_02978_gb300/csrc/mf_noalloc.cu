@@ -2,24 +2,26 @@
 // covariance of every partition) for callers that cannot allocate device
 // memory.
 //
-// Some callers of this library run where no device allocation may happen
-// once they are up: code replayed inside a captured CUDA graph whose memory
-// plan is fixed, real-time flight or ground-segment pipelines that forbid
+// Some callers of this library may not allocate device memory once they are
+// running: real-time flight or ground-segment pipelines that forbid any
 // allocation after start-up, and hosts whose device memory is owned by
 // another allocator (a framework's caching pool, an embedded runtime) that
-// this library cannot call.  They cannot create a plan (mf_plan allocates
-// its workspace), so this entry point keeps the per-block partial moments in
-// a fixed file-scope device array instead.
+// this library cannot call.  They cannot create a plan (mf_plan allocates its
+// workspace), so this entry point keeps the per-block partial moments in a
+// fixed file-scope device array instead.
 //
 // That array is a __device__ global: every GPU that loads the library holds
 // its kNoAllocScratchBytes (64 MiB) until the process exits.  In host code
 // its name is only a host-side stand-in, not a device address, so the first
 // call on each device looks up the device address with cudaGetSymbolAddress
-// (with that device current) and caches it; make that first call before any
-// stream capture.  Every call shares the array and leaves the last call's
-// contents behind: each call clears what must start at zero (the status
-// words), and calls that overlap on the GPU (different streams, or several
-// host threads) race on it.
+// (with that device current) and caches it, together with the kernels'
+// shared-memory limits; make that first call before any stream capture.  The
+// cached address belongs to the device's primary context: a process that
+// resets the device (cudaDeviceReset) must not call this entry point again.
+// Every call shares the array and leaves the last call's contents behind:
+// each call rewrites the line table and clears the status words (what must
+// start at zero), and calls that overlap on the GPU (different streams, or
+// several host threads) race on it.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -45,6 +47,11 @@ struct DeviceScratch {
 };
 std::mutex g_mutex;
 DeviceScratch g_devices[kMaxDevices];
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;  // set under g_mutex
+
+// the line table of one call, written by the device from a kernel argument
+// (no host staging buffer whose lifetime the copy would depend on)
+__global__ void write_line_kernel(mf::LineInfo* dst, mf::LineInfo line) { *dst = line; }
 
 mf_status fail(mf_status s, const std::string& msg) {
   mf::set_last_error(msg);
@@ -66,15 +73,24 @@ int nj_bucket(int B4) {
 mf_status setup_device(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_mutex);
   if (dev < 0 || dev >= kMaxDevices) return fail(MF_ERR_UNSUPPORTED, "device index out of range");
+  if (!g_encode) {
+    void* fp = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fp, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return fail(MF_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fp);
+  }
   DeviceScratch& d = g_devices[dev];
   if (!d.ready) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess)
       return fail(MF_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    const int bmax = mf::kMaxB, ba = (bmax + 6) / 4 * 4;
+    const int bmax = mf::kMaxB, ba = mf::aug_width(bmax, mf::kMaxDirs);
     for (int nj : {1, 2, 4, 6, 8, 9, 10, 12, 16}) {
-      e = mf::stats_set_attributes(nj, mf::stats_smem_bytes(8 * nj));
+      e = mf::stats_set_attributes(nj, mf::stats_smem_bytes(8 * nj, mf::kDirsFp32));
       if (e != cudaSuccess) break;
     }
     if (e == cudaSuccess) e = mf::background_set_attributes(mf::background_smem_bytes(bmax, ba));
@@ -87,17 +103,10 @@ mf_status setup_device(int dev, unsigned char** out) {
   return MF_OK;
 }
 
+// (after setup_device, which resolved g_encode)
 bool encode_map(CUtensorMap* m, const mf::Params& p, const float* cube) {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return false;
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-  }
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = g_encode;
+  if (!fn) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)p.bands_total, (cuuint64_t)p.cols, (cuuint64_t)p.rows};
   const cuuint64_t strides[2] = {(cuuint64_t)p.bands_total * sizeof(float),
                                  (cuuint64_t)p.bands_total * p.cols * sizeof(float)};
@@ -138,16 +147,20 @@ extern "C" mf_status mf_background_noalloc(const mf_desc* d, const float* cube,
   p.Pl = (p.cols + p.G - 1) / p.G;
   p.P = p.Pl;
   p.n_lines = 1;
-  p.BA = (B + 6) / 4 * 4;
+  p.K = mf::kDirsFp32;
+  p.BA = mf::aug_width(B, p.K);
   p.flags = d->flags;
   p.cube = cube;
   p.mask = mask;
 
-  // scratch layout: line table (1) | pilot (P, B) float | status (P) int | moments
+  // scratch layout: line table (1) | directions (P, K, B), offsets (P, K),
+  // scales (P, K) float | status (P) int | moments
   const size_t P = (size_t)p.P;
   const size_t K1E = (size_t)mf::k1_entries(p.BA);
   const size_t line_bytes = align256(sizeof(mf::LineInfo));
-  const size_t fixed = line_bytes + align256(P * B * sizeof(float)) + align256(P * sizeof(int));
+  const size_t dir_bytes = align256(P * p.K * B * sizeof(float));
+  const size_t off_bytes = align256(P * p.K * sizeof(float));
+  const size_t fixed = line_bytes + dir_bytes + 2 * off_bytes + align256(P * sizeof(int));
   const size_t per_chunk = P * p.G * K1E * sizeof(float2);  // one row chunk per column
   if (fixed + per_chunk > kNoAllocScratchBytes) {
     char msg[256];
@@ -175,19 +188,21 @@ extern "C" mf_status mf_background_noalloc(const mf_desc* d, const float* cube,
   if (st != MF_OK) return st;
   p.lines = reinterpret_cast<const mf::LineInfo*>(base);
   p.pilot = reinterpret_cast<float*>(base + line_bytes);
-  p.status = reinterpret_cast<int*>(base + line_bytes + align256(P * B * sizeof(float)));
+  p.pilot_c = reinterpret_cast<float*>(base + line_bytes + dir_bytes);
+  p.pilot_s = reinterpret_cast<float*>(base + line_bytes + dir_bytes + off_bytes);
+  p.status = reinterpret_cast<int*>(base + line_bytes + dir_bytes + 2 * off_bytes);
   p.k1part = reinterpret_cast<float2*>(base + fixed);
 
   CUtensorMap map;
   if (!encode_map(&map, p, cube)) return fail(MF_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the line table from the stack: a copy from pageable memory returns once
-  // the data is staged
-  e = cudaMemcpyAsync(base, &line, sizeof line, cudaMemcpyHostToDevice, s);
+  write_line_kernel<<<1, 1, 0, s>>>(reinterpret_cast<mf::LineInfo*>(base), line);
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemsetAsync(p.status, 0, P * sizeof(int), s);
   if (e != cudaSuccess) return fail(MF_ERR_CUDA, std::string("set-up copies: ") + cudaGetErrorString(e));
   const int nj = nj_bucket(p.B4);
-  mf::stats_launch(nj, p.n_items, mf::stats_smem_bytes(B), s, map, p, mf::STAT_INIT, 0);
+  mf::pilot_dirs_launch(s, p);
+  mf::stats_launch(nj, p.n_items, mf::stats_smem_bytes(B, p.K), s, map, p, mf::STAT_INIT, 0);
   mf::background_launch(mf::background_smem_bytes(B, p.BA), s, p, mu0, cov0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MF_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));

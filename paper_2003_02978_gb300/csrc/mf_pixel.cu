@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_abort;
   __shared__ int s_failed[kTileCols];
+  __shared__ __align__(8) uint64_t s_never;  // fault hook: a barrier nothing arrives on
 
   const int li = line_of_block(p, blockIdx.x);
   const LineInfo line = p.lines[li];
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
       mbar_init(&full[q], 1);
       mbar_init(&empty[q], kStageRows);
     }
+    mbar_init(&s_never, 1);
     mbar_fence_init();
   }
   __syncthreads();
@@ -190,7 +192,17 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
   float a_nx;
   int m_nx;
   fetch(0, a_nx, m_nx);
-  for (int i = 0; i < nst; ++i) {
+  // fault hook (MF_FAULT=timeout): in pass 0 every warp makes one bounded
+  // wait on a barrier that nothing arrives on; it runs out, and the CTA
+  // leaves through the timeout path below (which first waits for the copies
+  // it issued) instead of streaming its rows
+  if (p.test_wait > 0 && pass == 0) {
+    if (!__all_sync(0xffffffffu, mbar_wait_for(&s_never, 0, p.test_wait)) && lane == 0)
+      atomicExch(&s_abort, 1);
+    __syncthreads();
+  }
+  const int nst_run = s_abort ? 0 : nst;
+  for (int i = 0; i < nst_run; ++i) {
     const int sq = i % kPixStages;
     // refill the previous stage's buffer once every warp has read it
     if (tid == 0 && i >= 1 && i - 1 + kPixStages < nst) {

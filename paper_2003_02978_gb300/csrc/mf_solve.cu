@@ -119,54 +119,44 @@ __device__ void reduce_k1(const Params& p, int part, const DfMat& A) {
   __syncthreads();
 }
 
-// C = (1/N) sum (e + a u1 + b u2 + u3)(...)^T from the augmented moments
-// G (symmetric in A), written into the upper triangle (diagonal included)
-// of A's leading B x B block; the border rows B.. of A are read, not
-// written.  With P_i, R_i, Q_i the coefficients of u1_j, u2_j, u3_j,
-//   C_ij N = G_ij + u1_j P_i + u2_j R_i + u3_j Q_i
-//          + u1_i G_ja + u2_i G_jb + u3_i G_j1,
-//   P_i = G_ia + G_aa u1_i + G_ab u2_i + G_a1 u3_i   (R_i, Q_i likewise),
-// the same sum of terms as expanding the outer product.  u2 == nullptr
-// means u2 = 0 (the initial statistics).  scratch: 3 B double-floats.
-__device__ void assemble(const Params& p, const DfMat& A, const df* u1, const df* u2, const df* u3,
-                         df invN, double* S_out, df* scratch) {
-  const int B = p.B;
+// C = (1/N) sum (e + sum_k a_k q_k + b u_b + u_1)(...)^T from the augmented
+// moments G of [e, a_1 .. a_K, b, 1] (symmetric in A; coefficient column c
+// at row / column B + c, c < W = K + 2), written into the upper triangle
+// (diagonal included) of A's leading B x B block; the border rows B.. of A
+// are read, not written.  The coefficient vectors are T_c = q_c (c < K,
+// float, K x B in Q), T_K = u_b (null: zero, the initial statistics) and
+// T_{K+1} = u_1.  With
+//   P_ic = G_ic + sum_d G_cd T_id,
+//   C_ij N = G_ij + sum_c (T_jc P_ic + T_ic G_jc),
+// the same sum of terms as expanding the outer product.  scratch: W B
+// double-floats.
+__device__ void assemble(const Params& p, const DfMat& A, const float* Q, const df* ub,
+                         const df* u1, df invN, double* S_out, df* scratch) {
+  const int B = p.B, K = p.K, W = K + 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const df zero{0.f, 0.f};
-  auto Ga = [&](int i) { return A.get(B, i); };
-  auto Gb = [&](int i) { return A.get(B + 1, i); };
-  auto G1 = [&](int i) { return A.get(B + 2, i); };
-  const df aa = Ga(B), ab = Ga(B + 1), a1 = Ga(B + 2);
-  const df bb = Gb(B + 1), b1 = Gb(B + 2), n1 = G1(B + 2);
+  auto T = [&](int c, int i) -> df {
+    if (c < K) return df{Q[c * B + i], 0.f};
+    return c == K ? ub[i] : u1[i];
+  };
   df* P = scratch;
-  df* R = P + B;
-  df* Q = R + B;
-  for (int i = tid; i < B; i += kThreads) {
-    df pa = df_fma(a1, u3[i], df_fma(aa, u1[i], Ga(i)));
-    df q1 = df_fma(n1, u3[i], df_fma(a1, u1[i], G1(i)));
-    df rb = zero;
-    if (u2) {
-      pa = df_fma(ab, u2[i], pa);
-      q1 = df_fma(b1, u2[i], q1);
-      rb = df_fma(b1, u3[i], df_fma(bb, u2[i], df_fma(ab, u1[i], Gb(i))));
+  for (int idx = tid; idx < W * B; idx += kThreads) {
+    const int c = idx / B, i = idx - c * B;
+    if (c == K && !ub) continue;
+    df v = A.get(B + c, i);
+    for (int d = 0; d < W; ++d) {
+      if (d == K && !ub) continue;
+      v = df_fma(A.get(B + c, B + d), T(d, i), v);
     }
-    P[i] = pa;
-    R[i] = rb;
-    Q[i] = q1;
+    P[idx] = v;
   }
   __syncthreads();
   for (int j = warp; j < B; j += kWarps) {
-    const df u1j = u1[j], u3j = u3[j], Gaj = Ga(j), G1j = G1(j);
-    const df u2j = u2 ? u2[j] : zero, Gbj = Gb(j);
     for (int i = j + lane; i < B; i += 32) {
       df v = A.get(j, i);  // G_ji = G_ij
-      v = df_fma(u1j, P[i], v);
-      v = df_fma(u3j, Q[i], v);
-      v = df_fma(u1[i], Gaj, v);
-      v = df_fma(u3[i], G1j, v);
-      if (u2) {
-        v = df_fma(u2j, R[i], v);
-        v = df_fma(u2[i], Gbj, v);
+      for (int c = 0; c < W; ++c) {
+        if (c == K && !ub) continue;
+        v = df_fma(T(c, j), P[c * B + i], v);
+        v = df_fma(T(c, i), A.get(B + c, j), v);
       }
       v = df_mul(v, invN);
       A.set(j, i, v);
@@ -176,6 +166,28 @@ __device__ void assemble(const Params& p, const DfMat& A, const df* u1, const df
         S_out[(size_t)j * B + i] = d;
       }
     }
+  }
+  __syncthreads();
+}
+
+// The partition's directions q_k into shared memory (Q, K x B floats) and
+// w = sum_k c_k q_k, and from the reduced moments the mean
+//   mu = w + (sum_i e_i + sum_k (sum_i a_ik) q_k) / N;
+// u1 = w - mu (the constant column of the initial statistics).
+__device__ void init_mean(const Params& p, int part, const DfMat& A, df invN, float* Q, df* mu,
+                          df* u1) {
+  const int B = p.B, K = p.K, cc = B + K + 1;
+  for (int q = threadIdx.x; q < K * B; q += kThreads) Q[q] = p.pilot[(size_t)part * K * B + q];
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += kThreads) {
+    df w{0.f, 0.f}, sa = A.get(b, cc);
+    for (int k = 0; k < K; ++k) {
+      const df qk{Q[k * B + b], 0.f};
+      w = df_fma(df{p.pilot_c[(size_t)part * K + k], 0.f}, qk, w);
+      sa = df_fma(A.get(B + k, cc), qk, sa);
+    }
+    mu[b] = df_add(w, df_mul(sa, invN));
+    u1[b] = df_sub(w, mu[b]);
   }
   __syncthreads();
 }
@@ -204,13 +216,17 @@ __device__ void fail_partition(const Params& p, int part, bool init) {
 }  // namespace
 
 size_t solve_init_smem_bytes(int B, int BA) {
-  return ((size_t)BA * BA + 12 * (size_t)B) * sizeof(df) + 64;
+  const int K = BA - B;  // at most the directions + 2 of the augmented width (upper bound)
+  return ((size_t)BA * BA + (8 + K + 2) * (size_t)B) * sizeof(df) + (size_t)K * B * sizeof(float) +
+         64;
 }
 size_t solve_iter_smem_bytes(int B) {
   return ((size_t)B * linv_ld(B) + 16 * (size_t)B + 8) * sizeof(df) + 64;
 }
 size_t solve_literal_smem_bytes(int B, int BA) {
-  return ((size_t)BA * BA + 10 * (size_t)B) * sizeof(df) + 64;
+  const int K = BA - B;
+  return ((size_t)BA * BA + (6 + K + 2) * (size_t)B) * sizeof(df) + (size_t)K * B * sizeof(float) +
+         64;
 }
 
 __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
@@ -218,35 +234,30 @@ __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
   __shared__ df red[kWarps];
   const int part = blockIdx.x;
   const int tid = threadIdx.x;
-  const int B = p.B, BA = p.BA;
+  const int B = p.B, BA = p.BA, K = p.K;
   const size_t pb = (size_t)part * B;
   const DfMat A{reinterpret_cast<float*>(smem_raw), BA, BA * BA};
-  df* vm = reinterpret_cast<df*>(smem_raw) + (size_t)BA * BA;  // pilot m
-  df* vmu = vm + B;              // mu^0
-  df* vu3 = vmu + B;             // m - mu^0, later mu^0 - mu0f
+  df* vmu = reinterpret_cast<df*>(smem_raw) + (size_t)BA * BA;  // mu^0
+  df* vu3 = vmu + B;             // sum c_k q_k - mu^0, later mu^0 - mu0f
   df* vt = vu3 + B;              // t^0
   df* vy = vt + B;
   df* vz = vy + B;
   df* invd = vz + B;
   df* vmf = invd + B;            // mu0f
-  df* scr = vmf + B;             // 3 B: assemble's coefficient vectors
+  df* scr = vmf + B;             // (K + 2) B: assemble's scratch
+  float* vq = reinterpret_cast<float*>(scr + (size_t)(K + 2) * B);  // directions, K x B
   if (p.status[part] != MF_OK) return;  // the statistics pass timed out
+  if (p.fault_notspd) {  // fault hook (MF_FAULT=notspd)
+    fail_partition(p, part, true);
+    return;
+  }
 
   reduce_k1(p, part, A);
-  const df N = A.get(B + 2, B + 2);
+  const df N = A.get(B + K + 1, B + K + 1);
   const bool enough = N.hi > (float)B;
   const df invN = enough ? df_recip(N) : df{0.f, 0.f};
-  const df sa = A.get(B, B + 2);
-  for (int b = tid; b < B; b += kThreads) {
-    const float m = p.pilot[pb + b];
-    vm[b] = df{m, 0.f};
-    // mu^0 = m + (sum e + (sum a) m) / N
-    const df mu = df_add(df{m, 0.f}, df_mul(df_fma(sa, df{m, 0.f}, A.get(b, B + 2)), invN));
-    vmu[b] = mu;
-    vu3[b] = df_sub(df{m, 0.f}, mu);
-  }
-  __syncthreads();
-  assemble(p, A, vm, nullptr, vu3, invN, p.S + (size_t)part * B * B, scr);
+  init_mean(p, part, A, invN, vq, vmu, vu3);
+  assemble(p, A, vq, nullptr, vu3, invN, p.S + (size_t)part * B * B, scr);
   const bool ok = enough && chol_inv_df(A, B, invd);
   if (!ok) {
     fail_partition(p, part, true);
@@ -600,36 +611,49 @@ __global__ void __launch_bounds__(kThreads, 4) solve_literal_kernel(Params p, in
   __shared__ df red[kWarps];
   const int part = blockIdx.x;
   const int tid = threadIdx.x;
-  const int B = p.B, BA = p.BA;
+  const int B = p.B, BA = p.BA, K = p.K;
   const size_t pb = (size_t)part * B;
   if (p.status[part] != MF_OK) return;
   if (pass > p.lines[part_line(p, part)].n_iter) return;  // the line's iterations are done
   const DfMat A{reinterpret_cast<float*>(smem_raw), BA, BA * BA};
   df* u1 = reinterpret_cast<df*>(smem_raw) + (size_t)BA * BA;  // mu0f
   df* u2 = u1 + B;               // t^k
-  df* u3 = u2 + B;               // mu0f - mu^k
+  df* u3 = u2 + B;               // sum c_k q_k - mu^k
   df* vz = u3 + B;
   df* invd = vz + B;
   df* vd = invd + B;             // mu^k - mu0f
+  df* scr = vd + B;              // (K + 2) B: assemble's scratch, later the solve's
+  float* vq = reinterpret_cast<float*>(scr + (size_t)(K + 2) * B);  // directions, K x B
 
   reduce_k1(p, part, A);
-  const df N = A.get(B + 2, B + 2);
+  const df N = A.get(B + K + 1, B + K + 1);
   const df invN = df_recip(N);
+  // the statistics kernel's split of this pass: along mu0f with offset 1 for
+  // one direction (the tensor-core form), along the initial directions q_k
+  // with their offsets c_k otherwise
+  for (int q = tid; q < K * B; q += kThreads)
+    vq[q] = K == 1 ? p.mu0f[pb + q] : p.pilot[(size_t)part * K * B + q];
+  __syncthreads();
   for (int b = tid; b < B; b += kThreads) {
     const df mf{p.mu0f[pb + b], 0.f};
     const df mk = ldf(p.muk, pb + b);
+    df w{0.f, 0.f};
+    for (int k = 0; k < K; ++k) {
+      const float ck = K == 1 ? 1.f : p.pilot_c[(size_t)part * K + k];
+      w = df_fma(df{ck, 0.f}, df{vq[k * B + b], 0.f}, w);
+    }
     u1[b] = mf;
     u2[b] = ldf(p.tprev, pb + b);
-    u3[b] = df_sub(mf, mk);
+    u3[b] = df_sub(w, mk);
     vd[b] = df_sub(mk, mf);
   }
   __syncthreads();
-  assemble(p, A, u1, u2, u3, invN, nullptr, vd + B);
+  assemble(p, A, vq, u2, u3, invN, nullptr, scr);
   if (!chol_inv_df(A, B, invd)) {
     fail_partition(p, part, false);
     return;
   }
-  xtx_apply_df(A, B, invd, u2, vd + B, vz);
+  xtx_apply_df(A, B, invd, u2, scr, vz);
   const df q = block_dot_df(u2, vz, B, red);
   const df muv = block_dot_df(u1, vz, B, red);
   const df coff = block_dot_df(vd, vz, B, red);
@@ -651,13 +675,13 @@ __global__ void __launch_bounds__(kThreads) background_kernel(Params p, double* 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int part = blockIdx.x;
   const int tid = threadIdx.x;
-  const int B = p.B, BA = p.BA;
+  const int B = p.B, BA = p.BA, K = p.K;
   const size_t pb = (size_t)part * B;
   const DfMat A{reinterpret_cast<float*>(smem_raw), BA, BA * BA};
-  df* vm = reinterpret_cast<df*>(smem_raw) + (size_t)BA * BA;
-  df* vmu = vm + B;
+  df* vmu = reinterpret_cast<df*>(smem_raw) + (size_t)BA * BA;
   df* vu3 = vmu + B;
-  df* scr = vu3 + B;  // 3 B: assemble's coefficient vectors
+  df* scr = vu3 + B;  // (K + 2) B: assemble's scratch
+  float* vq = reinterpret_cast<float*>(scr + (size_t)(K + 2) * B);
   double* cov = cov_out + (size_t)part * B * B;
   if (p.status[part] != MF_OK) {
     for (int idx = tid; idx < B * B; idx += kThreads) cov[idx] = __longlong_as_double(0x7ff8000000000000LL);
@@ -665,19 +689,11 @@ __global__ void __launch_bounds__(kThreads) background_kernel(Params p, double* 
     return;
   }
   reduce_k1(p, part, A);
-  const df N = A.get(B + 2, B + 2);
+  const df N = A.get(B + K + 1, B + K + 1);
   const bool enough = N.hi > (float)B;
   const df invN = enough ? df_recip(N) : df{0.f, 0.f};
-  const df sa = A.get(B, B + 2);
-  for (int b = tid; b < B; b += kThreads) {
-    const float m = p.pilot[pb + b];
-    vm[b] = df{m, 0.f};
-    const df mu = df_add(df{m, 0.f}, df_mul(df_fma(sa, df{m, 0.f}, A.get(b, B + 2)), invN));
-    vmu[b] = mu;
-    vu3[b] = df_sub(df{m, 0.f}, mu);
-  }
-  __syncthreads();
-  assemble(p, A, vm, nullptr, vu3, invN, cov, scr);
+  init_mean(p, part, A, invN, vq, vmu, vu3);
+  assemble(p, A, vq, nullptr, vu3, invN, cov, scr);
   for (int b = tid; b < B; b += kThreads)
     mu_out[pb + b] = enough ? df_to_double(vmu[b]) : __longlong_as_double(0x7ff8000000000000LL);
   if (!enough)
@@ -685,7 +701,9 @@ __global__ void __launch_bounds__(kThreads) background_kernel(Params p, double* 
 }
 
 size_t background_smem_bytes(int B, int BA) {
-  return ((size_t)BA * BA + 6 * (size_t)B) * sizeof(df) + 64;
+  const int K = BA - B;
+  return ((size_t)BA * BA + (2 + K + 2) * (size_t)B) * sizeof(df) + (size_t)K * B * sizeof(float) +
+         64;
 }
 cudaError_t background_set_attributes(size_t smem) {
   return cudaFuncSetAttribute(background_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -7,15 +7,21 @@
 //
 // One CTA streams one detector column over a chunk of rows: a TMA box of 128
 // rows x B bands per stage, double buffered on mbarriers.  Each pixel is
-// split along a reference direction m (the first valid pixel of the
-// partition at initialisation, mu^0 afterwards):
-//   x_i = rho_i m + e_i,  rho_i = x_i.m / m.m,
-// which removes the large albedo component (Sec. II-C) from what is
-// accumulated in float32.  The CTA forms the augmented second moments of
-//   [e_i, a_i, b_i, 1],  a_i = rho_i - 1,  b_i = -r_i alpha_i^{k-1},
-// a symmetric (B+3)x(B+3) product in 4x4 register blocks, folded every 32
+// split along the partition's K reference directions q_k (pilot_dirs_kernel:
+// an orthonormal basis of its first valid pixels, which spans the albedo
+// direction of Sec. II-C and the strongest background modes):
+//   x_i = sum_k rho_ik q_k + e_i,  rho_ik = (x_i . q_k) / (q_k . q_k),
+// so that what is accumulated in float32 is small: the residual e_i and the
+// centred coefficients a_ik = rho_ik - c_k.  With a covariance whose
+// condition number reaches 1e7, float32 products of the unsplit pixels (or
+// of a one-direction split) leave errors of 1e-4 to 1e-3 relative along the
+// smallest eigenvectors; with K = 8 directions they are below 1e-6.  The CTA
+// forms the augmented second moments of
+//   u_i = [e_i, a_i1 .. a_iK, b_i, 1],  b_i = -r_i alpha_i^{k-1},
+// a symmetric BA x BA product in 4x4 register blocks, folded every 32
 // pixels into double-float (TwoSum) accumulators, and writes them out.  The
-// solve kernel reduces them and assembles C exactly.
+// solve kernels reduce them and assemble C exactly from
+//   x_i - mu = e_i + sum_k a_ik q_k + b_i t + (sum_k c_k q_k - mu).
 #include "mf_common.cuh"
 #include "mf_pixel_io.cuh"
 #include "mf_tma.cuh"
@@ -36,48 +42,166 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 
 struct StatSmem {
   size_t stage_bytes, stages_off, coef_off, acc_off, bar_off, total;
+  int ncb;  // float4 groups of a pixel's coefficients [a_1 .. a_K, b, 1, 0 ..]
 };
-// stages | coefficients [a, b, 1, 0] | double-float accumulators | barriers
-__host__ __device__ inline StatSmem stat_layout(int B) {
+// stages | coefficients | double-float accumulators | barriers.  One
+// coefficient buffer suffices: a stage's coefficients are written (phase A)
+// only after the previous stage's products (phase B) are done.
+__host__ __device__ inline StatSmem stat_layout(int B, int K) {
   StatSmem L;
-  const int nb = (B + 4) / 4;
+  const int BA = aug_width(B, K);
+  const int nb = BA / 4;
   const size_t nblk = (size_t)nb * (nb + 1) / 2;
+  L.ncb = (BA - B) / 4;
   L.stage_bytes = (size_t)kStatRows * B * sizeof(float);
   L.stages_off = 0;
   L.coef_off = 2 * L.stage_bytes;
-  L.acc_off = L.coef_off + 2 * (size_t)kStatRows * 4 * sizeof(float);
+  L.acc_off = L.coef_off + (size_t)kStatRows * L.ncb * 4 * sizeof(float);
   L.bar_off = L.acc_off + nblk * 32 * sizeof(float);
   L.total = L.bar_off + 4 * sizeof(uint64_t);
   return L;
 }
 }  // namespace
 
-size_t stats_smem_bytes(int B) { return stat_layout(B).total + 128; }
+size_t stats_smem_bytes(int B, int K) { return stat_layout(B, K).total + 128; }
+
+// Reference directions of the float32 statistics split: an orthonormal basis
+// q_1 .. q_K of the partition's first valid pixels (row-major over its
+// columns), by modified Gram-Schmidt with one re-orthogonalisation in
+// float64, rounded to float32; s_k = 1 / (q_k . q_k) of the rounded q_k and
+// c_k = (q_k . m) s_k, m the mean of the pixels examined.  A pixel that adds
+// no new direction (its residual below 1e-6 of its norm) is passed over; if
+// fewer than K independent pixels exist the remaining q_k, s_k, c_k are 0.
+// Any directions give the same moments in exact arithmetic: these keep what
+// is accumulated in float32 small.  One warp per partition.
+__global__ void pilot_dirs_kernel(Params p) {
+  const int part = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (part >= p.P) return;
+  const int K = p.K, B = p.B;
+  const LineInfo line = p.lines[part_line(p, part)];
+  const int c0 = part_col0(p, part), ncp = part_ncols(p, part);
+  const long total = (long)line.rows * ncp;
+  constexpr int kQ = kMaxB / 32;  // this lane's bands lane + 32 j
+  double q[kMaxDirs][kQ];
+  double mean[kQ];
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    mean[j] = 0.0;
+#pragma unroll
+    for (int k = 0; k < kMaxDirs; ++k) q[k][j] = 0.0;
+  }
+  auto wsum = [](double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  };
+  int n = 0, seen = 0;  // warp-uniform
+  for (long base = 0; base < total && n < K; base += 32) {
+    const long i = base + lane;
+    bool ok = false;
+    if (i < total) {
+      const int row = line.row0 + (int)(i / ncp), col = c0 + (int)(i % ncp);
+      ok = !p.mask || p.mask[(size_t)row * p.cols + col] == 0;
+      if (ok) {
+        const float4* px = reinterpret_cast<const float4*>(pixel_ptr(p, row, col));
+        for (int f = 0; f < p.B4; ++f) ok = ok && finite4(__ldg(px + f));
+      }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, ok);
+    while (bal && n < K) {
+      const long v = base + __ffs(bal) - 1;
+      bal &= bal - 1;
+      const float* px = pixel_ptr(p, line.row0 + (int)(v / ncp), c0 + (int)(v % ncp));
+      double x[kQ];
+#pragma unroll
+      for (int j = 0; j < kQ; ++j) {
+        const int b = lane + 32 * j;
+        x[j] = b < B ? (double)px[b] : 0.0;
+        mean[j] += x[j];
+      }
+      ++seen;
+      double xn2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < kQ; ++j) xn2 += x[j] * x[j];
+      xn2 = wsum(xn2);
+      for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+        for (int k = 0; k < kMaxDirs; ++k) {
+          if (k >= n) break;
+          double d = 0.0;
+#pragma unroll
+          for (int j = 0; j < kQ; ++j) d += q[k][j] * x[j];
+          d = wsum(d);
+#pragma unroll
+          for (int j = 0; j < kQ; ++j) x[j] -= d * q[k][j];
+        }
+      double r2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < kQ; ++j) r2 += x[j] * x[j];
+      r2 = wsum(r2);
+      if (r2 > 1e-12 * xn2 && r2 > 0.0) {
+        const double inv = 1.0 / sqrt(r2);
+#pragma unroll
+        for (int k = 0; k < kMaxDirs; ++k)
+          if (k == n)
+#pragma unroll
+            for (int j = 0; j < kQ; ++j) q[k][j] = x[j] * inv;
+        ++n;
+      }
+    }
+  }
+  const double inv_seen = seen > 0 ? 1.0 / seen : 0.0;
+#pragma unroll
+  for (int k = 0; k < kMaxDirs; ++k) {
+    if (k >= K) break;
+    double qq = 0.0, qm = 0.0;
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) {
+      const int b = lane + 32 * j;
+      const float qf = (k < n && b < B) ? (float)q[k][j] : 0.f;
+      if (b < B) p.pilot[((size_t)part * K + k) * B + b] = qf;
+      qq += (double)qf * qf;
+      qm += (double)qf * (mean[j] * inv_seen);
+    }
+    qq = wsum(qq);
+    qm = wsum(qm);
+    if (lane == 0) {
+      const double sk = qq > 0.0 ? 1.0 / qq : 0.0;
+      p.pilot_s[(size_t)part * K + k] = (float)sk;
+      p.pilot_c[(size_t)part * K + k] = (float)(qm * sk);
+    }
+  }
+}
+
+void pilot_dirs_launch(cudaStream_t s, const Params& p) {
+  pilot_dirs_kernel<<<(p.P + 3) / 4, 128, 0, s>>>(p);
+}
+
+static_assert(kMaxDirs + 2 <= 12, "a pixel's coefficients fill at most three float4 groups");
 
 template <int NJ>
 __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__ CUtensorMap map,
                                                          Params p, int mode, int pass) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(16) float s_ref[kMaxB];
-  __shared__ float s_inv_ref2;
-  __shared__ int s_pilot, s_abort;
+  __shared__ __align__(16) float s_dir[kMaxDirs * kMaxB];   // q_k, k < K
+  __shared__ __align__(16) float s_mu0f[kMaxB];             // literal: mu^0 for r_i
+  __shared__ float s_dc[kMaxDirs], s_ds[kMaxDirs];          // c_k, s_k
+  __shared__ int s_abort;
 
   const StatItem it = stat_item(p, blockIdx.x);
   const LineInfo line = p.lines[it.line];
   // literal schedule: lines whose iterations are done take no part
   if (mode == STAT_LITERAL && pass > line.n_iter) return;
   const int c = it.c;
-  const int chunk = it.chunk;
   const int part = part_of(p, it.line, c);
-  const int c0 = part_col0(p, part);
-  const int ncp = part_ncols(p, part);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int B = p.B, B4 = p.B4, BA = p.BA;
-  const StatSmem L = stat_layout(B);
+  const int B = p.B, B4 = p.B4, BA = p.BA, K = p.K;
+  const StatSmem L = stat_layout(B, K);
+  const int ncb = L.ncb;
   float* stage[2] = {reinterpret_cast<float*>(smem_raw + L.stages_off),
                      reinterpret_cast<float*>(smem_raw + L.stages_off + L.stage_bytes)};
-  float4* coef[2] = {reinterpret_cast<float4*>(smem_raw + L.coef_off),
-                     reinterpret_cast<float4*>(smem_raw + L.coef_off) + kStatRows};
+  float4* coef = reinterpret_cast<float4*>(smem_raw + L.coef_off);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bar_off);
 
   const int r_beg = it.r_beg;
@@ -102,52 +226,21 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
     }
   }
 
-  // ---- reference direction m
-  if (mode == STAT_INIT) {
-    if (warp == 0) {
-      // first valid pixel of the partition (its line's rows) in row-major order
-      long found = -1;
-      const long total = (long)line.rows * ncp;
-      for (long base = 0; base < total && found < 0; base += 32) {
-        const long i = base + lane;
-        bool ok = false;
-        if (i < total) {
-          const int row = line.row0 + (int)(i / ncp), col = c0 + (int)(i % ncp);
-          ok = !p.mask || p.mask[(size_t)row * p.cols + col] == 0;
-          if (ok) {
-            const float4* px = reinterpret_cast<const float4*>(pixel_ptr(p, row, col));
-            for (int f = 0; f < B4; ++f) ok = ok && finite4(__ldg(px + f));
-          }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, ok);
-        if (bal) found = base + __ffs(bal) - 1;
-      }
-      if (lane == 0) s_pilot = (int)found;
-    }
-    __syncthreads();
-    const int pi = s_pilot;
-    for (int b = tid; b < B; b += kThreads) {
-      float v = 0.f;
-      if (pi >= 0) v = pixel_ptr(p, line.row0 + pi / ncp, c0 + pi % ncp)[b];
-      s_ref[b] = v;
-      if (c == c0 && chunk == 0) p.pilot[(size_t)part * B + b] = v;
-    }
-  } else {
-    for (int b = tid; b < B; b += kThreads) s_ref[b] = p.mu0f[(size_t)part * B + b];
+  // ---- the partition's reference directions (pilot_dirs_kernel), and for
+  // the literal schedule mu^0 (the albedo factor of the b coefficient)
+  // (one direction in the literal schedule: mu^0 with offset 1, whose
+  // coefficient is the albedo factor; the solve kernel assembles likewise)
+  const bool lit1 = mode == STAT_LITERAL && K == 1;
+  for (int q = tid; q < K * B; q += kThreads)
+    s_dir[q] = lit1 ? p.mu0f[(size_t)part * B + q] : p.pilot[(size_t)part * K * B + q];
+  if (tid < K) {
+    s_dc[tid] = lit1 ? 1.f : p.pilot_c[(size_t)part * K + tid];
+    s_ds[tid] = lit1 ? p.pscal[(size_t)part * PS_N + PS_INVMU2] : p.pilot_s[(size_t)part * K + tid];
   }
+  if (mode == STAT_LITERAL)
+    for (int b = tid; b < B; b += kThreads) s_mu0f[b] = p.mu0f[(size_t)part * B + b];
   __syncthreads();
-  if (tid == 0) {
-    if (mode == STAT_INIT) {
-      double n2 = 0.0;
-      for (int b = 0; b < B; ++b) n2 += (double)s_ref[b] * s_ref[b];
-      s_inv_ref2 = n2 > 0.0 ? (float)(1.0 / n2) : 0.f;
-    } else {
-      s_inv_ref2 = p.pscal[(size_t)part * PS_N + PS_INVMU2];
-    }
-  }
-  __syncthreads();
-  const float inv_ref2 = s_inv_ref2;
-  const float4* ref4 = reinterpret_cast<const float4*>(s_ref);
+  const float inv_mu2 = mode == STAT_LITERAL ? p.pscal[(size_t)part * PS_N + PS_INVMU2] : 0.f;
   const bool albedo = (p.flags & MF_ALBEDO) != 0;
 
   // ---- SYRK ownership: 4x4 blocks of the upper triangle, blocks tid,
@@ -155,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
   // with the 32 floats (16 hi, 16 lo) of a block strided by nblk
   const int nb = BA / 4;
   const int nblk = nb * (nb + 1) / 2;
-  const int bcoef = B / 4;  // block index of [a, b, 1, 0]
+  const int bcoef = B / 4;  // first block of the coefficients
   float* accs = reinterpret_cast<float*>(smem_raw + L.acc_off);
   for (int q = tid; q < nblk * 32; q += kThreads) accs[q] = 0.f;
 
@@ -168,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
     }
     __syncthreads();
     if (s_abort) break;
-    // phase A: residuals e_i in place, coefficients [a, b, 1, 0]
+    // phase A: residuals e_i in place, coefficients [a_1 .. a_K, b, 1, 0 ..]
     {
       const int row = r_beg + i * kStatRows + slot;
       const bool inb = row < r_end;
@@ -177,8 +270,19 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
       const bool fin = lds_pixel<NJ>(px, inb, e, B4, x);
       const size_t pix = (size_t)(inb ? row : 0) * p.cols + c;
       const bool valid = inb && fin && (!p.mask || p.mask[pix] == 0);
-      const float rho = pair_dot<NJ>(x, ref4, e, B4) * inv_ref2;
-      split_residual<NJ>(x, ref4, rho, e, B4);
+      float r_alb = 1.f;
+      if (mode == STAT_LITERAL && albedo)
+        r_alb = pair_dot<NJ>(x, reinterpret_cast<const float4*>(s_mu0f), e, B4) * inv_mu2;
+      // coefficients on the unsplit pixel, then one subtraction per direction
+      float rho[kMaxDirs];
+#pragma unroll
+      for (int k = 0; k < kMaxDirs; ++k)
+        rho[k] = k < K ? pair_dot<NJ>(x, reinterpret_cast<const float4*>(s_dir + k * B), e, B4) *
+                             s_ds[k]
+                       : 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxDirs; ++k)
+        if (k < K) split_residual<NJ>(x, reinterpret_cast<const float4*>(s_dir + k * B), rho[k], e, B4);
       if (!valid) {
 #pragma unroll
         for (int j = 0; j < NJ; ++j) x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -186,12 +290,20 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
       sts_pixel<NJ>(px, e, B4, x);
       if (e == 0) {
         float bcf = 0.f;
-        if (mode == STAT_LITERAL && valid) {
-          const float r = albedo ? rho : 1.f;
-          bcf = r > 0.f ? -(r * p.alpha[pix]) : 0.f;
+        if (mode == STAT_LITERAL && valid) bcf = r_alb > 0.f ? -(r_alb * p.alpha[pix]) : 0.f;
+        float cf[4 * 3];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          float v = 0.f;
+          if (q < K) v = rho[q] - s_dc[q];
+          else if (q == K) v = bcf;
+          else if (q == K + 1) v = 1.f;
+          cf[q] = valid ? v : 0.f;
         }
-        coef[sb][slot] = valid ? make_float4(rho - 1.f, bcf, 1.f, 0.f)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+          if (g < ncb)
+            coef[slot * ncb + g] = make_float4(cf[4 * g], cf[4 * g + 1], cf[4 * g + 2], cf[4 * g + 3]);
       }
     }
     __syncthreads();
@@ -199,11 +311,12 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
     for (int blk = tid; blk < nblk; blk += kThreads) {
       int bi, bj;
       block_of(blk, nb, bi, bj);
-      // row pointers and strides: the [a, b, 1, 0] block lives in coef[]
-      const float* pa = (bi == bcoef) ? reinterpret_cast<const float*>(coef[sb]) : stage[sb] + 4 * bi;
-      const float* pb = (bj == bcoef) ? reinterpret_cast<const float*>(coef[sb]) : stage[sb] + 4 * bj;
-      const int sa = (bi == bcoef) ? 4 : B;
-      const int sbs = (bj == bcoef) ? 4 : B;
+      // row pointers and strides: the coefficient blocks live in coef[]
+      const float* cbase = reinterpret_cast<const float*>(coef);
+      const float* pa = (bi >= bcoef) ? cbase + 4 * (bi - bcoef) : stage[sb] + 4 * bi;
+      const float* pb = (bj >= bcoef) ? cbase + 4 * (bj - bcoef) : stage[sb] + 4 * bj;
+      const int sa = (bi >= bcoef) ? 4 * ncb : B;
+      const int sbs = (bj >= bcoef) ? 4 * ncb : B;
       float hi[16], lo[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {

@@ -166,9 +166,20 @@ __global__ void pilot_kernel(Params p) {
     }
   }
   const float inv = n > 0 ? 1.f / (float)n : 0.f;
+  float n2 = 0.f;
 #pragma unroll
   for (int q = 0; q < kMaxB / 32; ++q)
-    if (lane + 32 * q < p.B) p.pilot[(size_t)part * p.B + lane + 32 * q] = sum[q] * inv;
+    if (lane + 32 * q < p.B) {
+      const float m = sum[q] * inv;
+      p.pilot[(size_t)part * p.B + lane + 32 * q] = m;
+      n2 = fmaf(m, m, n2);
+    }
+  n2 = warp_sumf(n2);
+  // one direction, offset 1: the coefficient a = rho - 1 of the split
+  if (lane == 0) {
+    p.pilot_c[part] = 1.f;
+    p.pilot_s[part] = n2 > 0.f ? 1.f / n2 : 0.f;
+  }
 }
 
 // named barrier 1 among the converter warps.  It follows code where only

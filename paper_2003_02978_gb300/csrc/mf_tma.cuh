@@ -54,6 +54,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
+// the same with a caller's limit in SM clock cycles
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long cycles) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > cycles) return false;
+  }
+  return true;
+}
+
 // generic-proxy writes to shared memory -> later async-proxy (TMA) writes
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

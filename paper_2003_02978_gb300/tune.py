@@ -68,9 +68,12 @@ def _time(plan, cube, k, lam, eps, n_iter, mask, reps):
 
 
 def autotune(cube, k, lam, eps, n_iter, mask=None, line_rows=None, band_lo=0, band_hi=None,
-             col_group=1, flags=3, precision=0, reps=3, use_cache=True, verbose=False):
+             col_group=1, flags=3, precision=0, reps=3, use_cache=True, verbose=False,
+             candidates=None):
     """Best {pixel_rows, stat_rows} for this cube's shape (a dict for the
-    ``tuning`` argument of Plan / BatchPlan), timing candidates on the cube."""
+    ``tuning`` argument of Plan / BatchPlan), timing candidates on the cube.
+    ``candidates``: optional (pixel_rows, stat_rows) pairs to try instead of
+    the full grid PIXEL_ROWS x STAT_ROWS."""
     rows, cols, bt = cube.shape
     band_hi = bt if band_hi is None else band_hi
     line_rows = [rows] if line_rows is None else list(line_rows)
@@ -78,22 +81,23 @@ def autotune(cube, k, lam, eps, n_iter, mask=None, line_rows=None, band_lo=0, ba
     cache = load_cache() if use_cache else {}
     if key in cache:
         return dict(cache[key]["tuning"])
-    stat_rows = [s for s in STAT_ROWS if not (precision == 1 and s > 1024)]
+    if candidates is None:
+        candidates = [(pr, sr) for pr in PIXEL_ROWS for sr in STAT_ROWS]
+    candidates = [(pr, sr) for pr, sr in candidates if not (precision == 1 and sr > 1024)]
     results = []
-    for pr in PIXEL_ROWS:
-        for sr in stat_rows:
-            t = {"pixel_rows": pr, "stat_rows": sr}
-            if len(line_rows) == 1:
-                plan = Plan(rows, cols, bt, band_lo, band_hi, col_group, flags, precision,
-                            tuning=t)
-            else:
-                plan = BatchPlan(line_rows, cols, bt, band_lo, band_hi, col_group, flags,
-                                 precision, tuning=t)
-            ms = _time(plan, cube, k, lam, eps, n_iter, mask, reps)
-            plan.close()
-            results.append((ms, t))
-            if verbose:
-                print(f"  pixel_rows={pr:5d} stat_rows={sr:5d}: {ms:.3f} ms")
+    for pr, sr in candidates:
+        t = {"pixel_rows": pr, "stat_rows": sr}
+        if len(line_rows) == 1:
+            plan = Plan(rows, cols, bt, band_lo, band_hi, col_group, flags, precision,
+                        tuning=t)
+        else:
+            plan = BatchPlan(line_rows, cols, bt, band_lo, band_hi, col_group, flags,
+                             precision, tuning=t)
+        ms = _time(plan, cube, k, lam, eps, n_iter, mask, reps)
+        plan.close()
+        results.append((ms, t))
+        if verbose:
+            print(f"  pixel_rows={pr:5d} stat_rows={sr:5d}: {ms:.3f} ms")
     ms, best = min(results, key=lambda r: r[0])
     if use_cache:
         cache[key] = {"tuning": best, "ms": ms,

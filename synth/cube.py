@@ -121,11 +121,14 @@ def make_scene(rows: int, cols: int, bands: int = 72, *, n_plumes: int = 1,
                mask_col_frac=None, cond: float = 1e4, snr=(100.0, 500.0),
                albedo_sigma: float = 0.2, seed: int = 0, device="cpu",
                nan_masked: bool = False, keep_truth: bool = True,
-               forward_model: str = "linear") -> Scene:
+               forward_model: str = "linear", out=None, mask_out=None) -> Scene:
     """Draw one scene.  ``device`` is where the cube is generated (torch
     Philox on CUDA, torch CPU generator otherwise).  ``forward_model``:
     "linear" (first-order Beer-Lambert, the model the filter assumes) or
-    "exp" (the unlinearised Beer-Lambert transmittance)."""
+    "exp" (the unlinearised Beer-Lambert transmittance).  ``out`` /
+    ``mask_out``: optional contiguous (rows, cols, bands) float32 and
+    (rows, cols) uint8 tensors on ``device`` to draw into (for example row
+    slices of one stacked batch), instead of new ones."""
     if forward_model not in ("linear", "exp"):
         raise ValueError("forward_model must be 'linear' or 'exp'")
     wl = wavelengths(bands)
@@ -145,7 +148,11 @@ def make_scene(rows: int, cols: int, bands: int = 72, *, n_plumes: int = 1,
     mu_t = torch.as_tensor(mu_bg, dtype=f32, device=dev)
     k_t = torch.as_tensor(k, dtype=f32, device=dev)
     gain_t = torch.as_tensor(gain, dtype=f32, device=dev)
-    cube = torch.empty((rows, cols, bands), dtype=f32, device=dev)
+    if out is not None:
+        assert tuple(out.shape) == (rows, cols, bands) and out.dtype == f32 and out.is_contiguous()
+        cube = out
+    else:
+        cube = torch.empty((rows, cols, bands), dtype=f32, device=dev)
     albedo = torch.empty((rows, cols), dtype=f32, device=dev)
     chunk = max(1, (1 << 24) // max(1, cols * bands))
     alpha_t = torch.as_tensor(alpha, dtype=f32, device=dev)
@@ -172,6 +179,9 @@ def make_scene(rows: int, cols: int, bands: int = 72, *, n_plumes: int = 1,
             mask = (u < mask_frac).to(torch.uint8)
         if nan_masked:
             cube[mask.bool()] = float("nan")
+        if mask_out is not None:
+            mask_out.copy_(mask)
+            mask = mask_out
     C_bg = U @ U.T + np.diag(sigma ** 2)
     return Scene(cube=cube, k=k, mask=mask, alpha_true=alpha if keep_truth else None,
                  albedo=albedo.cpu().numpy() if keep_truth and rows * cols <= (1 << 24) else None,

@@ -10,8 +10,13 @@ TOL_FP32 = 1e-4
 # ceiling on the amplification factor that may widen one pixel's bound: a
 # pixel amplified more than this is still checked, at this factor
 AMP_CAP = 1e3
-# at most this fraction of the valid pixels (rounded up) may use the widening,
-# i.e. miss the plain bound tol * max|ref|
+# pixels with A_i > AMP_STRONG are the strongly amplified ones: at most
+# AMP_FRAC of the valid pixels may be (a property of the scene and the
+# iteration count, checked so that the widening cannot cover a large share)
+AMP_STRONG = 10.0
+AMP_FRAC = 1e-2
+# of the other pixels (A_i <= AMP_STRONG) at most this fraction (rounded up)
+# may use the widening, i.e. miss the plain bound tol * max|ref|
 WIDEN_FRAC = 1e-4
 
 
@@ -34,8 +39,9 @@ def f32(a):
 def alpha_report(got, ref, valid, amp, tol=TOL_FP32):
     """Every figure of the parity bar (see ``check_alpha``) without asserting:
     e_inf, e_2, e_sc (the error scaled by the capped amplification factor),
-    n_valid, n_amp (pixels with A_i > 10), max_amp, n_widened (pixels beyond
-    the plain bound tol * max|ref|) and n_widen_max (how many may be)."""
+    n_valid, n_amp (pixels with A_i > AMP_STRONG), max_amp, n_widened (pixels
+    with A_i <= AMP_STRONG beyond the plain bound tol * max|ref|) and
+    n_widen_max (how many of those may be)."""
     g = np.asarray(got, dtype=np.float64)[valid]
     r = np.asarray(ref, dtype=np.float64)[valid]
     a = np.asarray(amp, dtype=np.float64)[valid]
@@ -44,8 +50,8 @@ def alpha_report(got, ref, valid, amp, tol=TOL_FP32):
     d = np.abs(g - r)
     e_sc = float((d / (scale * np.minimum(a, AMP_CAP))).max()) if r.size else 0.0
     return {"e_inf": e_inf, "e_2": e_2, "e_sc": e_sc, "n_valid": int(r.size),
-            "n_amp": int((a > 10).sum()), "max_amp": float(a.max()) if r.size else 1.0,
-            "n_widened": int((d > tol * scale).sum()),
+            "n_amp": int((a > AMP_STRONG).sum()), "max_amp": float(a.max()) if r.size else 1.0,
+            "n_widened": int(((d > tol * scale) & (a <= AMP_STRONG)).sum()),
             "n_widen_max": int(math.ceil(WIDEN_FRAC * r.size))}
 
 
@@ -59,15 +65,17 @@ def check_alpha(got, ref, valid, amp, tol=TOL_FP32):
       the previous estimate was tiny and positive any rounding is magnified,
       in every precision.  A_i is capped at AMP_CAP, so no pixel goes
       unchecked;
-    * at most ceil(WIDEN_FRAC * n_valid) pixels may use that widening, i.e.
-      exceed the plain bound tol * max|ref|: an error spread over many
-      moderately amplified pixels fails.
+    * at most AMP_FRAC of the pixels may be strongly amplified (A_i >
+      AMP_STRONG), and of the others at most ceil(WIDEN_FRAC * n_valid) may
+      use the widening, i.e. exceed the plain bound tol * max|ref|: an error
+      spread over many mildly amplified pixels fails.
     Returns the dict of ``alpha_report``."""
     rep = alpha_report(got, ref, valid, amp, tol)
     info = (f"(e_inf {rep['e_inf']:.3e}, e_2 {rep['e_2']:.3e}, {rep['n_amp']} of "
-            f"{rep['n_valid']} pixels with A > 10, max A {rep['max_amp']:.3g}, "
-            f"{rep['n_widened']} beyond the plain bound, at most {rep['n_widen_max']})")
+            f"{rep['n_valid']} pixels with A > {AMP_STRONG:g}, max A {rep['max_amp']:.3g}, "
+            f"{rep['n_widened']} others beyond the plain bound, at most {rep['n_widen_max']})")
     assert rep["e_2"] <= tol, f"e_2 {rep['e_2']:.3e} > {tol} {info}"
     assert rep["e_sc"] <= tol, f"amplification-scaled e_inf {rep['e_sc']:.3e} > {tol} {info}"
+    assert rep["n_amp"] <= AMP_FRAC * rep["n_valid"], f"too many amplified pixels {info}"
     assert rep["n_widened"] <= rep["n_widen_max"], f"too many widened pixels {info}"
     return rep

@@ -4,7 +4,7 @@ check a pixel whose amplification factor is enormous."""
 import numpy as np
 import pytest
 
-from parity import AMP_CAP, TOL_FP32, alpha_report, check_alpha
+from parity import AMP_CAP, AMP_FRAC, TOL_FP32, alpha_report, check_alpha
 
 
 def _case(n=20000, seed=0):
@@ -22,11 +22,11 @@ def test_clean_result_passes():
 
 
 def test_error_spread_over_amplified_pixels_fails():
-    """Every pixel amplified 50-fold, 0.5% of them wrong by twice the plain
-    bound: each pixel is inside its widened bound and e_2 stays below the
-    bar, but far more than 1e-4 of the pixels use the widening."""
+    """Every pixel mildly amplified (5-fold), 0.5% of them wrong by twice the
+    plain bound: each pixel is inside its widened bound and e_2 stays below
+    the bar, but far more than 1e-4 of the pixels use the widening."""
     ref, valid = _case()
-    amp = np.full_like(ref, 50.0)
+    amp = np.full_like(ref, 5.0)
     scale = np.abs(ref).max()
     got = ref.copy()
     idx = np.arange(0, ref.size, 200)           # 0.5% of the pixels, each wrong by
@@ -53,4 +53,14 @@ def test_huge_amplification_is_capped():
         check_alpha(got, ref, valid, amp)
     got[7] = ref[7] + 0.5 * AMP_CAP * TOL_FP32 * scale
     rep = check_alpha(got, ref, valid, amp)
-    assert rep["n_widened"] == 1 and rep["n_widen_max"] == 400
+    assert rep["n_widened"] == 0 and rep["n_amp"] == 1 and rep["n_widen_max"] == 400
+
+
+def test_strong_amplification_of_many_pixels_fails():
+    """A widening that would cover more than AMP_FRAC of the pixels (each
+    amplified 50-fold) is refused even when every error is within it."""
+    ref, valid = _case()
+    amp = np.ones_like(ref)
+    amp[: int(2 * AMP_FRAC * ref.size)] = 50.0
+    with pytest.raises(AssertionError, match="amplified pixels"):
+        check_alpha(ref.copy(), ref, valid, amp)
