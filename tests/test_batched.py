@@ -141,3 +141,27 @@ def test_batch_rejects_bad_rows():
     import paper_2003_02978_gb300 as mfg
     with pytest.raises(mfg.MFError):
         mfg.BatchPlan([100, 0, 50], 4, 72)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_per_column_mask_fraction(precision):
+    """Lines drawn like the batched workload (synth.batched_lines): per-column
+    masked fraction U(0, 0.3), lambda log-uniform in [1e-4, 1e-2], N_iter in
+    5..20; shorter lines and fewer columns so that the oracle checks every
+    partition.  Lines keep at least 1500 rows, so that every partition has
+    the 1000 valid pixels the BF16-split bound is stated for."""
+    from synth import batched_lines, make_scene
+    lines = batched_lines(4, cols=12, rows_range=(1500, 3000), seed=3)
+    scenes = [make_scene(ln["rows"], 12, 72, n_plumes=3, plume_sigma=(3.0, 8.0),
+                         plume_peak=(500.0, 5000.0), mask_col_frac=ln["mask_col_frac"],
+                         seed=ln["seed"]) for ln in lines]
+    cube = torch.cat([s.cube for s in scenes], 0).contiguous()
+    mask = torch.cat([s.mask for s in scenes], 0).contiguous()
+    k = f32(scenes[0].k)
+    rows = [ln["rows"] for ln in lines]
+    lams = [ln["lam"] for ln in lines]
+    nits = [ln["n_iter"] for ln in lines]
+    got, status, slices, P = run_batch(rows, 12, 72, cube, mask, k, lams, nits,
+                                       precision=precision)
+    assert P == 4 * 12 and np.all(status == 0)
+    check_lines(scenes, cube, mask, k, got, status, slices, lams, nits, ALBEDO | SPARSE, TOL_FP32)
