@@ -283,16 +283,25 @@ def oracle_one_thread(cube, mask, k, lam, eps, n_iter):
 
 def alpha_figures(got, ref, valid):
     """e_inf = max|got - ref| / max|ref|, e_2 = ||got - ref|| / ||ref|| over
-    the valid pixels, and how many exceed 1e-4 * max|ref|."""
+    the valid pixels, how many differ by more than 1e-4 * max|ref|, and the
+    zero-flips among those (one side exactly 0: the clamp max(0, .) of a
+    near-threshold pixel went the other way, after which the reweighting's
+    zero is sticky) with e_inf and e_2 over the other pixels."""
     g = np.asarray(got, np.float64)[valid]
     r = np.asarray(ref, np.float64)[valid]
     if r.size == 0:
         return {"e_inf": 0.0, "e_2": 0.0, "n_valid": 0, "n_over_1e-4": 0}
     d = np.abs(g - r)
     scale = max(np.abs(r).max(), 1e-30)
-    return {"e_inf": float(d.max() / scale),
-            "e_2": float(np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-30)),
-            "n_valid": int(r.size), "n_over_1e-4": int((d > 1e-4 * scale).sum())}
+    nr = max(np.linalg.norm(r), 1e-30)
+    over = d > 1e-4 * scale
+    flips = over & ((g == 0) | (r == 0))
+    keep = ~flips
+    return {"e_inf": float(d.max() / scale), "e_2": float(np.linalg.norm(g - r) / nr),
+            "n_valid": int(r.size), "n_over_1e-4": int(over.sum()),
+            "n_zero_flips": int(flips.sum()),
+            "e_inf_excl_flips": float(d[keep].max() / scale) if keep.any() else 0.0,
+            "e_2_excl_flips": float(np.linalg.norm(d[keep]) / nr)}
 
 
 def covariance_figures(cov_gpu, mu_gpu, X):

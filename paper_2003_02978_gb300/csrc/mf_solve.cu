@@ -384,8 +384,17 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
   const int nunits = part_ncols(p, part) * line.n_rb;
   const float* P0 = p.k3part + (size_t)(line.k3u0 + (long long)part_col0(p, part) * line.n_rb) * K3E;
   for (int t = tid; t < B + 4; t += kThreads) {
+    // eight loads in flight, then their fixed-order sum
     df s{0.f, 0.f};
-    for (int u = 0; u < nunits; ++u) s = df_addf(s, P0[(size_t)u * K3E + t]);
+    int u = 0;
+    for (; u + 8 <= nunits; u += 8) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = P0[(size_t)(u + q) * K3E + t];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s = df_addf(s, v[q]);
+    }
+    for (; u < nunits; ++u) s = df_addf(s, P0[(size_t)u * K3E + t]);
     mom[t] = s;
   }
   __syncthreads();

@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from parity import TOL_FP32, check_alpha, f32
+from parity import TOL_FP32, check_alpha, f32, retrieve_near_threshold
 from synth import make_scene
 
 pytestmark = pytest.mark.gpu
@@ -46,7 +46,7 @@ def run_batch(line_rows, cols, bands, cube, mask, k, lams, n_iters, flags=ALBEDO
 
 
 def check_lines(scenes, cube, mask, k, got, status, slices, lams, n_iters, flags, tol,
-                col_group=1):
+                col_group=1, tol_pix=None):
     cube = cube.numpy()
     mask = mask.numpy()
     pl = -(-cube.shape[1] // col_group)
@@ -63,7 +63,9 @@ def check_lines(scenes, cube, mask, k, got, status, slices, lams, n_iters, flags
         amp = oracle.retrieve_amplification(sub.astype(np.float64), k, lams[li], 1e-9,
                                             n_iters[li], mask=msk, flags=flags,
                                             col_group=col_group)
-        check_alpha(got[sl], ref, ok, amp, tol)
+        near = retrieve_near_threshold(sub.astype(np.float64), k, lams[li], 1e-9, n_iters[li],
+                                       mask=msk, flags=flags, col_group=col_group)
+        check_alpha(got[sl], ref, ok, amp, tol, near=near, tol_pix=tol_pix)
 
 
 # (a line of 260 rows, 3.6 samples per band, leaves C so ill-conditioned that
@@ -152,6 +154,9 @@ def test_batch_per_column_mask_fraction(precision):
     the 1000 valid pixels the BF16-split bound is stated for."""
     from synth import batched_lines, make_scene
     lines = batched_lines(4, cols=12, rows_range=(1500, 3000), seed=3)
+    # the BF16-split form's stated per-pixel bound for partitions of 1000 to
+    # 2000 valid pixels: 2e-4 of max|alpha| (e_2 stays within 1e-4)
+    tol_pix = 2e-4 if precision else None
     scenes = [make_scene(ln["rows"], 12, 72, n_plumes=3, plume_sigma=(3.0, 8.0),
                          plume_peak=(500.0, 5000.0), mask_col_frac=ln["mask_col_frac"],
                          seed=ln["seed"]) for ln in lines]
@@ -164,4 +169,5 @@ def test_batch_per_column_mask_fraction(precision):
     got, status, slices, P = run_batch(rows, 12, 72, cube, mask, k, lams, nits,
                                        precision=precision)
     assert P == 4 * 12 and np.all(status == 0)
-    check_lines(scenes, cube, mask, k, got, status, slices, lams, nits, ALBEDO | SPARSE, TOL_FP32)
+    check_lines(scenes, cube, mask, k, got, status, slices, lams, nits, ALBEDO | SPARSE, TOL_FP32,
+                tol_pix=tol_pix)

@@ -19,7 +19,7 @@ import pytest
 import torch
 
 import oracle
-from parity import check_alpha, f32
+from parity import check_alpha, f32, retrieve_near_threshold
 from synth import workload_scene
 
 
@@ -91,4 +91,5 @@ def test_timeout_fault_reports_status_and_leaves_context_usable(monkeypatch, lib
     mask = sc.mask.numpy()
     ref, _ = oracle.retrieve(cube, f32(sc.k), prm["lam"], prm["eps"], 2, mask=mask)
     amp = oracle.retrieve_amplification(cube, f32(sc.k), prm["lam"], prm["eps"], 2, mask=mask)
-    check_alpha(a, ref, oracle.valid_pixels(sc.cube.numpy(), mask), amp)
+    near = retrieve_near_threshold(cube, f32(sc.k), prm["lam"], prm["eps"], 2, mask=mask)
+    check_alpha(a, ref, oracle.valid_pixels(sc.cube.numpy(), mask), amp, near=near)

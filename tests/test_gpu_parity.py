@@ -10,7 +10,7 @@ import pytest
 import torch
 
 import oracle
-from parity import TOL_FP32, alpha_errors, check_alpha, f32
+from parity import TOL_FP32, alpha_errors, check_alpha, f32, retrieve_near_threshold
 from synth import make_scene, workload_scene
 
 pytestmark = pytest.mark.gpu
@@ -66,11 +66,11 @@ def compare(cube_np, k, lam, eps, n_iter, mask=None, flags=ALBEDO | SPARSE, col_
     assert np.all(np.isnan(got[valid & failed]))
     ok = valid & ~failed
     assert np.all(np.isfinite(got[ok]))
-    amp = oracle.retrieve_amplification(cube_np.astype(np.float64), kk, lam, eps, n_iter,
-                                        mask=mask, band_lo=band_lo, band_hi=band_hi,
-                                        col_group=col_group, flags=flags,
-                                        alpha_init=None if alpha_init is None else f32(alpha_init))
-    rep = check_alpha(got, ref, ok, amp, tol)
+    akw = dict(mask=mask, band_lo=band_lo, band_hi=band_hi, col_group=col_group, flags=flags,
+               alpha_init=None if alpha_init is None else f32(alpha_init))
+    amp = oracle.retrieve_amplification(cube_np.astype(np.float64), kk, lam, eps, n_iter, **akw)
+    near = retrieve_near_threshold(cube_np.astype(np.float64), kk, lam, eps, n_iter, **akw)
+    rep = check_alpha(got, ref, ok, amp, tol, near=near)
     e_inf, e_2 = rep["e_inf"], rep["e_2"]
     if n_iter > 0:
         assert np.all(got[ok] >= 0.0)
@@ -214,7 +214,9 @@ def test_flightline_full_size_sampled_columns(flags):
     assert np.all(got[:, cols][~valid] == 0)
     amp = oracle.retrieve_amplification(sub.astype(np.float64), f32(sc.k), prm["lam"], prm["eps"],
                                         prm["n_iter"], mask=msk)
-    check_alpha(got[:, cols], ref, valid, amp)
+    near = retrieve_near_threshold(sub.astype(np.float64), f32(sc.k), prm["lam"], prm["eps"],
+                                   prm["n_iter"], mask=msk)
+    check_alpha(got[:, cols], ref, valid, amp, near=near)
 
 
 # ------------------------------------------------- BF16-split tensor-core form
@@ -349,4 +351,6 @@ def test_bf16split_flightline_sampled():
     valid = oracle.valid_pixels(sub, msk)
     amp = oracle.retrieve_amplification(sub.astype(np.float64), f32(sc.k), prm["lam"],
                                         prm["eps"], prm["n_iter"], mask=msk)
-    check_alpha(got[:, cols], ref, valid, amp, TOL_BF16SPLIT)
+    near = retrieve_near_threshold(sub.astype(np.float64), f32(sc.k), prm["lam"], prm["eps"],
+                                   prm["n_iter"], mask=msk)
+    check_alpha(got[:, cols], ref, valid, amp, TOL_BF16SPLIT, near=near)

@@ -64,3 +64,46 @@ def test_strong_amplification_of_many_pixels_fails():
     amp[: int(2 * AMP_FRAC * ref.size)] = 50.0
     with pytest.raises(AssertionError, match="amplified pixels"):
         check_alpha(ref.copy(), ref, valid, amp)
+
+
+def test_zero_flips_are_counted_and_capped():
+    """A near-threshold pixel where one side clamped to 0 and the other did
+    not is left out of e_2 and the per-pixel bound, but counted: at most
+    ceil(1e-4 n) of them."""
+    ref, valid = _case(n=20000)
+    got = ref.copy()
+    near = np.zeros_like(valid)
+    z = np.nonzero(ref == 0)[0][:3]
+    got[z] = 500.0                               # three pixels that stayed positive
+    near[z] = True
+    amp = np.ones_like(ref)
+    with pytest.raises(AssertionError):
+        check_alpha(got, ref, valid, amp)        # without the marking: a plain failure
+    with pytest.raises(AssertionError, match="zero-flips"):
+        check_alpha(got, ref, valid, amp, near=near)   # 3 > ceil(2)
+    got[z[2]] = 0.0
+    rep = check_alpha(got, ref, valid, amp, near=near)
+    assert rep["n_flips"] == 2 and rep["n_near"] == 3 and rep["e_2"] == 0.0
+
+
+def test_near_threshold_marks_the_flips_of_float32_sized_perturbations():
+    """The oracle on inputs perturbed by 1e-7 relative (float32 rounding)
+    clamps some pixels on the other side of zero than on the exact inputs;
+    every such zero-flip must be among the pixels ``near_threshold`` marks."""
+    import oracle
+    from parity import f32, near_threshold
+    from synth import workload_scene
+    sc, prm = workload_scene("flightline-4000x598x72", seed=3, cols=40)
+    cube = sc.cube.numpy().astype(np.float64)
+    valid = oracle.valid_pixels(cube, sc.mask.numpy())
+    flips = covered = 0
+    for c in range(cube.shape[1]):
+        X = cube[:, c][valid[:, c]]
+        Xp = X * (1 + 1e-7 * np.random.default_rng(c).standard_normal(X.shape))
+        a = oracle.retrieve_partition(X, f32(sc.k), prm["lam"], prm["eps"], 10)
+        b = oracle.retrieve_partition(Xp, f32(sc.k), prm["lam"], prm["eps"], 10)
+        near = near_threshold(X, f32(sc.k), prm["lam"], prm["eps"], 10)
+        flip = ((a == 0) | (b == 0)) & (np.abs(a - b) > 1e-6 * np.abs(a).max())
+        flips += int(flip.sum())
+        covered += int((flip & near).sum())
+    assert flips >= 1 and covered == flips, (flips, covered)

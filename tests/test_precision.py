@@ -24,7 +24,7 @@ import pytest
 import torch
 
 import oracle
-from parity import TOL_FP32, alpha_report, check_alpha, f32
+from parity import TOL_FP32, alpha_report, check_alpha, f32, retrieve_near_threshold
 from synth import workload_scene
 
 pytestmark = pytest.mark.gpu
@@ -57,6 +57,8 @@ def scene():
                               mask=msk)
     amp = oracle.retrieve_amplification(sub.astype(np.float64), kk, prm["lam"], prm["eps"],
                                         prm["n_iter"], mask=msk)
+    near = retrieve_near_threshold(sub.astype(np.float64), kk, prm["lam"], prm["eps"],
+                                   prm["n_iter"], mask=msk)
     valid = oracle.valid_pixels(sub, msk)
     stats = []
     for j in range(len(cols)):
@@ -65,7 +67,8 @@ def scene():
         C = oracle.covariance_about(X - m)
         ev, V = np.linalg.eigh(C)
         stats.append((m, C, ev, V))
-    yield dict(sc=sc, prm=prm, cols=cols, ref=ref, st=st, amp=amp, valid=valid, stats=stats)
+    yield dict(sc=sc, prm=prm, cols=cols, ref=ref, st=st, amp=amp, near=near, valid=valid,
+               stats=stats)
     del sc
     torch.cuda.empty_cache()
 
@@ -97,12 +100,12 @@ def test_fp32_at_condition_1e7(scene, flags):
     got, c_fro, c_eig = run_form(scene, flags, FP32)
     assert c_fro < C_FRO_FP32, c_fro
     assert c_eig < C_EIG_FP32, c_eig
-    check_alpha(got, scene["ref"], scene["valid"], scene["amp"], TOL_FP32)
+    check_alpha(got, scene["ref"], scene["valid"], scene["amp"], TOL_FP32, near=scene["near"])
 
 
 def test_bf16split_stated_bound_at_condition_1e7(scene):
     got, c_fro, c_eig = run_form(scene, ALBEDO | SPARSE, BF16SPLIT)
-    rep = alpha_report(got, scene["ref"], scene["valid"], scene["amp"])
+    rep = alpha_report(got, scene["ref"], scene["valid"], scene["amp"], near=scene["near"])
     assert c_fro < C_FRO_BF16, c_fro
     assert c_eig < C_EIG_BF16, c_eig
     assert rep["e_2"] < ALPHA_E2_BF16, rep

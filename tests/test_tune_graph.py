@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from parity import check_alpha, f32
+from parity import check_alpha, f32, retrieve_near_threshold
 from synth import workload_scene
 
 pytestmark = pytest.mark.gpu
@@ -50,7 +50,8 @@ def test_graph_recaptures_on_new_arguments():
         ref, _ = oracle.retrieve(cube, f32(sc.k), lam, prm["eps"], n)
         valid = oracle.valid_pixels(sc.cube.cpu().numpy(), None)
         amp = oracle.retrieve_amplification(cube, f32(sc.k), lam, prm["eps"], n)
-        check_alpha(got.cpu().numpy(), ref, valid, amp)
+        near = retrieve_near_threshold(cube, f32(sc.k), lam, prm["eps"], n)
+        check_alpha(got.cpu().numpy(), ref, valid, amp, near=near)
 
 
 def test_autotune_picks_a_candidate_and_caches(tmp_path, monkeypatch):
@@ -75,5 +76,6 @@ def test_autotune_picks_a_candidate_and_caches(tmp_path, monkeypatch):
     ref, _ = oracle.retrieve(cube, f32(sc.k), prm["lam"], prm["eps"], prm["n_iter"])
     valid = oracle.valid_pixels(sc.cube.cpu().numpy(), None)
     amp = oracle.retrieve_amplification(cube, f32(sc.k), prm["lam"], prm["eps"], prm["n_iter"])
-    check_alpha(a.cpu().numpy(), ref, valid, amp)
+    near = retrieve_near_threshold(cube, f32(sc.k), prm["lam"], prm["eps"], prm["n_iter"])
+    check_alpha(a.cpu().numpy(), ref, valid, amp, near=near)
     plan.close()
