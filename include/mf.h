@@ -268,7 +268,9 @@ mf_status mf_profile_read(mf_plan_t plan, double* ms, int64_t* launches, int32_t
  * The per-block partial moments live in a fixed 64 MiB file-scope device
  * array that every GPU loading the library holds until exit; shapes whose
  * moments do not fit (P * col_group * 8 * K bytes, K = 16 * nb (nb + 1) / 2,
- * nb = (B + 4) / 4; about 24 KB per detector column at B = 72) return
+ * nb = (B + 12) / 4: the bands, eight direction coefficients, the target
+ * coefficient and the constant, rounded up; about 30 KB per detector column
+ * at B = 72) return
  * MF_ERR_UNSUPPORTED and enqueue nothing.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress) and sets kernel
  * attributes: make it before any stream capture; after a cudaDeviceReset the
