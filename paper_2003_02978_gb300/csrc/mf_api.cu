@@ -325,6 +325,7 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   // form, kDirsFp32 for the float32 statistics
   p.K = d->precision == MF_BF16SPLIT ? 1 : mf::kDirsFp32;
   p.BA = mf::aug_width(B, p.K);
+  p.k1_colmajor = d->precision == MF_BF16SPLIT;
   p.flags = d->flags;
   p.n_lines = n_lines;
   pl->nj = nj_bucket(p.B4);
@@ -413,6 +414,7 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   }
   p.n_items = (int)items;
   p.n_blocks = (int)blocks;
+  p.line0 = pl->lines[0];
   pl->grid_stats = p.n_items;
   pl->grid_pixel = p.n_blocks;
   pl->smem_stats = d->precision == MF_BF16SPLIT ? mf::stats_tc_smem_bytes(B)

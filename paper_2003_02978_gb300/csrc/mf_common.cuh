@@ -20,7 +20,8 @@
 //              rows padded by one entry)
 //   pscal      (P, 4) float32        q, mu0f.v, (mu^k - mu0f).v, 1/(mu0f.mu0f)
 //   dscal      (P, 4) float64        N, mean(beta), q
-//   k1part     (P, G * n_sc, K1E) double-float   per-CTA augmented second moments
+//   k1part     (P, G * n_sc, K1E) double-float   per-CTA augmented second moments (the
+//              tensor-core form stores a column-major BA x BA float Q in each unit)
 //   k3part     (P, G * n_rb, K3E) float32        per-CTA enhancement moments
 //   status     (P) int32             mf_status per partition
 #pragma once
@@ -87,9 +88,14 @@ struct Params {
   long long test_wait;    // fault hook (MF_FAULT=timeout): > 0 makes every pixel CTA of
                           // pass 0 wait this many cycles on a barrier nothing arrives on
   int fault_notspd;       // fault hook (MF_FAULT=notspd): every initial factorisation fails
+  int k1_colmajor;        // moment units hold Q (BA x BA floats, column-major, G = Q + Q^T;
+                          // the tensor-core statistics) instead of the upper triangle of G in
+                          // 4 x 4 blocks of double-float pairs (the float32 statistics)
   double* energy;         // optional: (P, energy_stride) objective per iterate (null = off)
   int energy_stride;      // n_iter + 1
   const LineInfo* lines;  // device, n_lines
+  LineInfo line0;         // geometry of the only line of a single-line plan (its lambda and
+                          // N_iter fields are not kept current: read those from `lines`)
   // caller buffers
   const float* cube;
   const float* k;
@@ -194,8 +200,8 @@ struct StatItem {
 };
 __device__ __forceinline__ StatItem stat_item(const Params& p, int w) {
   StatItem it;
-  it.line = line_of_item(p, w);
-  const LineInfo L = p.lines[it.line];
+  it.line = p.n_lines == 1 ? 0 : line_of_item(p, w);
+  const LineInfo L = p.n_lines == 1 ? p.line0 : p.lines[it.line];
   const int local = w - L.item0;
   it.chunk = local / p.cols;
   it.c = local - it.chunk * p.cols;

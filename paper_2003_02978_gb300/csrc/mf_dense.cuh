@@ -212,7 +212,8 @@ __device__ __forceinline__ void panel_update_tile(const DfMat& A, const df* invd
 // lives in A's strict lower triangle (its unit diagonal is implicit).
 // Blocked right-looking over panels J of 8 rows [j0, j1):
 //  (a) one warp runs the panel's steps on its diagonal block only, giving
-//      U_JJ and W = L_JJ^{-1};
+//      U_JJ and W = L_JJ^{-1} (for the next panel, while the other warps
+//      finish (c) below the next panel's rows: a look-ahead);
 //  (b) the rest of the panel's rows is multiplied by W (the composite of
 //      the same steps and scalings): U_JK = W C_JK right of the block,
 //      X_JK = W R_JK left of it (R the identity half as updated so far);
@@ -233,14 +234,14 @@ __device__ inline bool chol_inv_df(const DfMat& A, int n, df* invd) {
     if (c < r) A.set(r, c, df{0.f, 0.f});
   }
   const int n4 = n >> 2;
+  __syncthreads();
+  // (a) of the first panel
+  if (tid < 32) {
+    const bool ok = factor_diag_block(A, 0, min(kPanel, n), invd);
+    if (tid == 0) s_fail = ok ? 0 : 1;
+  }
   for (int j0 = 0; j0 < n; j0 += kPanel) {
     const int j1 = min(j0 + kPanel, n), nb = j1 - j0;
-    __syncthreads();
-    // (a)
-    if (tid < 32) {
-      const bool ok = factor_diag_block(A, j0, j1, invd);
-      if (tid == 0) s_fail = ok ? 0 : 1;
-    }
     __syncthreads();
     if (s_fail) return false;
     // (b) slot = (row p of the panel, column pair outside the block); all
@@ -273,15 +274,30 @@ __device__ inline bool chol_inv_df(const DfMat& A, int n, df* invd) {
     __syncthreads();
     // (c) rows i >= j1: 4 x 4 tiles left of the panel's end (X) and on or
     // right of the diagonal (U), trailing row block I holding n4 - I of
-    // them; two slots (row pairs) per tile
+    // them; two slots (row pairs) per tile.  Look-ahead: first the next
+    // panel's rows (row blocks I < r1, a prefix of the slots), then one warp
+    // factors the next panel's diagonal block while the other warps update
+    // the remaining rows, which the next diagonal step does not touch.
     const int j4 = j1 >> 2, m = n4 - j4;
     const int tslots = 2 * (m * n4 - m * (m - 1) / 2);
-    for (int t = tid; t < tslots; t += kThreads) {
+    const int r1 = min(m, kPanel / 4);
+    const int t1 = 2 * (r1 * n4 - r1 * (r1 - 1) / 2);
+    auto tile = [&](int t) {
       int I, bj;
       tri_decode(t >> 1, n4, I, bj);
       const int u = bj - I, ib = j4 + I;
       const int kb = u < j4 ? u : ib + (u - j4);
       panel_update_tile(A, invd, j0, j1, 4 * ib + 2 * (t & 1), 4 * kb, kb == ib);
+    };
+    for (int t = tid; t < t1; t += kThreads) tile(t);
+    if (j1 < n) {
+      __syncthreads();
+      if (tid < 32) {
+        const bool ok = factor_diag_block(A, j1, min(j1 + kPanel, n), invd);
+        if (tid == 0) s_fail = ok ? 0 : 1;
+      } else {
+        for (int t = t1 + tid - 32; t < tslots; t += kThreads - 32) tile(t);
+      }
     }
   }
   __syncthreads();

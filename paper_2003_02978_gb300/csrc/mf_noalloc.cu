@@ -179,6 +179,7 @@ extern "C" mf_status mf_background_noalloc(const mf_desc* d, const float* cube,
   line.sc_rows = sc;
   line.n_sc = (p.rows + sc - 1) / sc;
   p.n_items = p.cols * line.n_sc;
+  p.line0 = line;
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

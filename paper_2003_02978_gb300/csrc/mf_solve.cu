@@ -88,6 +88,52 @@ __device__ void reduce_k1(const Params& p, int part, const DfMat& A) {
   const int nunits = part_ncols(p, part) * line.n_sc;
   const float2* P0 = p.k1part + (size_t)(line.k1u0 + (long long)part_col0(p, part) * line.n_sc) * K1E;
   constexpr int kU = 8;
+  if (p.k1_colmajor) {
+    // units of Q (column-major floats, BA x BA, BA a multiple of 4): R = the
+    // sum of the units' Q into A, two entries per load; then G = R + R^T in
+    // place
+    const float2* Q0 = P0;
+    const size_t ustride = K1E;  // float2 per unit
+    const int BB = BA * BA, BB2 = BB / 2;
+    for (int q0 = threadIdx.x; q0 < BB2; q0 += 2 * kThreads) {
+      df sx[2] = {df{0.f, 0.f}, df{0.f, 0.f}}, sy[2] = {df{0.f, 0.f}, df{0.f, 0.f}};
+      for (int u0 = 0; u0 < nunits; u0 += kU) {
+        float2 v[2][kU];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int k = 0; k < kU; ++k) {
+            const int q = q0 + h * kThreads, u = u0 + k;
+            v[h][k] = (q < BB2 && u < nunits) ? Q0[(size_t)u * ustride + q] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int k = 0; k < kU; ++k) {
+            sx[h] = df_addf(sx[h], v[h][k].x);
+            sy[h] = df_addf(sy[h], v[h][k].y);
+          }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = 2 * (q0 + h * kThreads);  // Q_mj at j BA + m
+        if (q < BB) {
+          A.set(q % BA, q / BA, sx[h]);
+          A.set((q + 1) % BA, (q + 1) / BA, sy[h]);
+        }
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < BB; idx += kThreads) {
+      const int a = idx / BA, b = idx - a * BA;
+      if (a > b) continue;
+      const df g = df_add(A.get(a, b), A.get(b, a));
+      A.set(a, b, g);
+      A.set(b, a, g);
+    }
+    __syncthreads();
+    return;
+  }
   for (int q0 = threadIdx.x; q0 < K1E; q0 += 2 * kThreads) {
     df sum[2] = {df{0.f, 0.f}, df{0.f, 0.f}};
     for (int u0 = 0; u0 < nunits; u0 += kU) {

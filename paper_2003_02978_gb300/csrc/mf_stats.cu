@@ -105,7 +105,8 @@ __global__ void pilot_dirs_kernel(Params p) {
       ok = !p.mask || p.mask[(size_t)row * p.cols + col] == 0;
       if (ok) {
         const float4* px = reinterpret_cast<const float4*>(pixel_ptr(p, row, col));
-        for (int f = 0; f < p.B4; ++f) ok = ok && finite4(__ldg(px + f));
+        // every band finite (the loads are independent: no short circuit)
+        for (int f = 0; f < p.B4; ++f) ok &= finite4(__ldg(px + f));
       }
     }
     unsigned bal = __ballot_sync(0xffffffffu, ok);

@@ -19,8 +19,9 @@
 // and an A operand is the first 128 columns from H's or L's start (the
 // columns past NP give rows of D that the epilogue ignores).  D accumulates in float32 in tensor memory;
 // the epilogue forms Q = (H^T H + L^T L) / 2 + H^T L, and G = Q + Q^T is
-// completed where the per-item moments are summed (each moment entry is
-// stored as the pair (Q_ab, Q_ba), read as their sum).
+// completed where the per-item moments are summed (each item's Q is stored
+// column-major, BA x BA floats, so that the stores of a warp are
+// contiguous).
 //
 // Persistent, warp-specialised kernel: one CTA per SM walks work items
 // (detector column, chunk of at most 1024 rows) of 128-pixel stages, with
@@ -151,19 +152,33 @@ __global__ void pilot_kernel(Params p) {
       ok = !p.mask || p.mask[(size_t)row * p.cols + col] == 0;
       if (ok) {
         const float4* px = reinterpret_cast<const float4*>(pixel_ptr(p, row, col));
-        for (int f = 0; f < p.B4; ++f) ok = ok && finite4(__ldg(px + f));
+        // every band finite (the loads are independent: no short circuit)
+        for (int f = 0; f < p.B4; ++f) ok &= finite4(__ldg(px + f));
       }
     }
     unsigned bal = __ballot_sync(0xffffffffu, ok);
-    while (bal && n < kPilot) {
-      const long v = base + __ffs(bal) - 1;
-      bal &= bal - 1;
-      const float* px = pixel_ptr(p, line.row0 + (int)(v / ncp), c0 + (int)(v % ncp));
+    // the batch's valid pixels (up to those still needed): all their loads
+    // first, then the sum in pixel order
+    float vals[kPilot][kMaxB / 32];
+    int cnt = 0;
 #pragma unroll
-      for (int q = 0; q < kMaxB / 32; ++q)
-        if (lane + 32 * q < p.B) sum[q] += px[lane + 32 * q];
-      ++n;
+    for (int j = 0; j < kPilot; ++j) {
+      if (bal && n + cnt < kPilot) {
+        const long v = base + __ffs(bal) - 1;
+        bal &= bal - 1;
+        const float* px = pixel_ptr(p, line.row0 + (int)(v / ncp), c0 + (int)(v % ncp));
+#pragma unroll
+        for (int q = 0; q < kMaxB / 32; ++q)
+          vals[j][q] = lane + 32 * q < p.B ? px[lane + 32 * q] : 0.f;
+        ++cnt;
+      }
     }
+#pragma unroll
+    for (int j = 0; j < kPilot; ++j)
+      if (j < cnt)
+#pragma unroll
+        for (int q = 0; q < kMaxB / 32; ++q) sum[q] += vals[j][q];
+    n += cnt;
   }
   const float inv = n > 0 ? 1.f / (float)n : 0.f;
   float n2 = 0.f;
@@ -326,11 +341,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int quad = warp & 3;            // a warp may access TMEM lanes 32 (warp % 4) ..
     const int m = quad * 32 + lane;       // row of G
     const int K1E = k1_entries(BA);
-    const int nb = BA / 4;
-    const int bi = m >> 2, u = m & 3;
-    // index of block (r, r) in the packed upper-triangular block list
-    auto blk_diag = [&](int r) { return r * nb - (r * (r - 1)) / 2; };
-    const int blk_row = blk_diag(bi);
     const uint32_t lanes = (uint32_t)(quad * 32) << 16;
     const uint32_t qsum = tmem + lanes + (uint32_t)(2 * L.accw);
     int g = 0;
@@ -338,8 +348,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       StatItem it;
       int nst;
       item_geom(w, it, nst);
-      // entry (a, b) of G = Q_ab + Q_ba: row m of Q gives the first term of
-      // the entries (m, j >= m's block) and the second of (j, m)
+      // the item's Q, BA x BA column-major (Q_mj at j BA + m): a warp's
+      // store of one column is 32 consecutive floats; the reduction forms
+      // G = Q + Q^T
       float* dst = reinterpret_cast<float*>(p.k1part + (size_t)it.unit * K1E);
       for (int s = 0; s < nst; ++s, ++g) {
         const int sb = g & 1;
@@ -383,10 +394,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
               const int j = c0 + k;
-              const int bj = j >> 2, v = j & 3;
-              if (j >= BA) continue;
-              if (bj >= bi) dst[2 * ((blk_row + (bj - bi)) * 16 + u * 4 + v)] = q[k];
-              if (bj <= bi) dst[2 * ((blk_diag(bj) + (bi - bj)) * 16 + v * 4 + u) + 1] = q[k];
+              if (j < BA) dst[(size_t)j * BA + m] = q[k];
             }
           }
         }
@@ -443,12 +451,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // the next item's is loaded into registers during the current item and
     // published by the named barrier that ends it
     const float* refsrc = (mode == STAT_INIT ? p.pilot : p.mu0f);
+    // ... and its 1 / (m . m) (the pilot's, or the plan's for mu^0), in the
+    // slot after the B entries
     auto ref_of = [&](int w) -> float {
-      if (w >= nitems || tid >= B) return 0.f;
+      if (w >= nitems || tid > B) return 0.f;
       const StatItem iw = stat_item(p, w);
-      return refsrc[(size_t)part_of(p, iw.line, iw.c) * B + tid];
+      const int pw_ = part_of(p, iw.line, iw.c);
+      if (tid < B) return refsrc[(size_t)pw_ * B + tid];
+      return mode == STAT_INIT ? p.pilot_s[pw_] : p.pscal[(size_t)pw_ * PS_N + PS_INVMU2];
     };
-    if (tid < B) s_ref[tid] = ref_of(blockIdx.x);
+    if (tid <= B) s_ref[tid] = ref_of(blockIdx.x);
     conv_bar();
     // every converter warp walks every item (and reaches every named barrier)
     // even after a failed wait; it only skips the work
@@ -456,18 +468,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       StatItem it;
       int nst;
       item_geom(w, it, nst);
-      const int part = part_of(p, it.line, it.c);
       const float* ref = s_ref + (t & 1) * (kMaxB + 4);
       const float ref_next = ref_of(w + gridDim.x);
-      float inv_ref2;
-      if (mode == STAT_INIT) {
-        float n2 = 0.f;
-        for (int b = lane; b < B; b += 32) n2 = fmaf(ref[b], ref[b], n2);
-        n2 = warp_sumf(n2);
-        inv_ref2 = n2 > 0.f ? 1.f / n2 : 0.f;
-      } else {
-        inv_ref2 = p.pscal[(size_t)part * PS_N + PS_INVMU2];
-      }
+      const float inv_ref2 = ref[B];
       // the lane's groups of the reference, in registers for the item
       float4 rf[NJ];
 #pragma unroll
@@ -557,7 +560,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&op_full[sb]);
       }
-      if (tid < B) s_ref[((t + 1) & 1) * (kMaxB + 4) + tid] = ref_next;
+      if (tid <= B) s_ref[((t + 1) & 1) * (kMaxB + 4) + tid] = ref_next;
       conv_bar();
     }
   }
