@@ -114,6 +114,38 @@ __device__ __forceinline__ void split_residual2(float4 (&x)[NJ], const float4 (&
     x[j] = make_float4(a.x, a.y, b.x, b.y);
   }
 }
+// pair_dot2 / split_residual2 with the reference in shared memory at the
+// lane's band groups f = e + 2 j (those past B4 are skipped)
+template <int NJ>
+__device__ __forceinline__ float pair_dot2s(const float4 (&x)[NJ], const float4* ref, int e, int B4) {
+  float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int f = e + 2 * j;
+    if (f < B4) {
+      const float4 r = ref[f];
+      d0 = __ffma2_rn(lo2(x[j]), lo2(r), d0);
+      d1 = __ffma2_rn(hi2(x[j]), hi2(r), d1);
+    }
+  }
+  const float d = (d0.x + d0.y) + (d1.x + d1.y);
+  return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+template <int NJ>
+__device__ __forceinline__ void split_residual2s(float4 (&x)[NJ], const float4* ref, float rho,
+                                                 int e, int B4) {
+  const float2 m = make_float2(-rho, -rho);
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int f = e + 2 * j;
+    if (f < B4) {
+      const float4 r = ref[f];
+      const float2 a = __ffma2_rn(m, lo2(r), lo2(x[j]));
+      const float2 b = __ffma2_rn(m, hi2(r), hi2(x[j]));
+      x[j] = make_float4(a.x, a.y, b.x, b.y);
+    }
+  }
+}
 // acc <- acc + s * x
 template <int NJ>
 __device__ __forceinline__ void axpy2(float4 (&acc)[NJ], float s, const float4 (&x)[NJ]) {

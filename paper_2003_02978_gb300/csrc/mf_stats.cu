@@ -273,17 +273,18 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
       const bool valid = inb && fin && (!p.mask || p.mask[pix] == 0);
       float r_alb = 1.f;
       if (mode == STAT_LITERAL && albedo)
-        r_alb = pair_dot<NJ>(x, reinterpret_cast<const float4*>(s_mu0f), e, B4) * inv_mu2;
+        r_alb = pair_dot2s<NJ>(x, reinterpret_cast<const float4*>(s_mu0f), e, B4) * inv_mu2;
       // coefficients on the unsplit pixel, then one subtraction per direction
       float rho[kMaxDirs];
 #pragma unroll
       for (int k = 0; k < kMaxDirs; ++k)
-        rho[k] = k < K ? pair_dot<NJ>(x, reinterpret_cast<const float4*>(s_dir + k * B), e, B4) *
+        rho[k] = k < K ? pair_dot2s<NJ>(x, reinterpret_cast<const float4*>(s_dir + k * B), e, B4) *
                              s_ds[k]
                        : 0.f;
 #pragma unroll
       for (int k = 0; k < kMaxDirs; ++k)
-        if (k < K) split_residual<NJ>(x, reinterpret_cast<const float4*>(s_dir + k * B), rho[k], e, B4);
+        if (k < K)
+          split_residual2s<NJ>(x, reinterpret_cast<const float4*>(s_dir + k * B), rho[k], e, B4);
       if (!valid) {
 #pragma unroll
         for (int j = 0; j < NJ; ++j) x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -325,22 +326,30 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
         lo[q] = accs[(16 + q) * nblk + blk];
       }
       for (int s0 = 0; s0 < kStatRows; s0 += kFold) {
-        float acc[16];
+        // the 4 x 4 products on the packed f32x2 pipe (fma.rn.f32x2, each
+        // element rounded as fmaf would): acc2[2 u + h] holds entries
+        // (u, 2 h) and (u, 2 h + 1)
+        float2 acc2[8];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+        for (int q = 0; q < 8; ++q) acc2[q] = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int s = s0; s < s0 + kFold; ++s) {
           const float4 va = *reinterpret_cast<const float4*>(pa + (size_t)s * sa);
           const float4 vb = *reinterpret_cast<const float4*>(pb + (size_t)s * sbs);
           const float a4[4] = {va.x, va.y, va.z, va.w};
-          const float b4[4] = {vb.x, vb.y, vb.z, vb.w};
+          const float2 b01 = make_float2(vb.x, vb.y), b23 = make_float2(vb.z, vb.w);
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int w = 0; w < 4; ++w) acc[u * 4 + w] = fmaf(a4[u], b4[w], acc[u * 4 + w]);
+          for (int u = 0; u < 4; ++u) {
+            const float2 au = make_float2(a4[u], a4[u]);
+            acc2[2 * u] = __ffma2_rn(au, b01, acc2[2 * u]);
+            acc2[2 * u + 1] = __ffma2_rn(au, b23, acc2[2 * u + 1]);
+          }
         }
 #pragma unroll
-        for (int q = 0; q < 16; ++q) two_sum_acc(hi[q], lo[q], acc[q]);
+        for (int q = 0; q < 8; ++q) {
+          two_sum_acc(hi[2 * q], lo[2 * q], acc2[q].x);
+          two_sum_acc(hi[2 * q + 1], lo[2 * q + 1], acc2[q].y);
+        }
       }
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
