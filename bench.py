@@ -706,6 +706,44 @@ def main():
         return prof
 
     prof = profiled(plan, prof_steps)
+
+    # --- the same split inside the timed configuration (one CUDA graph per
+    # retrieval): the library's device timeline, each launch from its first
+    # CTA's start to its last CTA's end on the GPU's global timer
+    def timeline(pl, steps):
+        pl.timeline(True)
+        run(pl)  # re-captures the graph with the probes
+        pl.timeline_read()
+        runs = []
+        for _ in range(steps):
+            run(pl)
+            runs.append(pl.timeline_read())
+        pl.timeline(False)
+        run(pl)  # and back to the probe-free graph
+        torch.cuda.synchronize(dev)
+        return runs
+
+    tl_runs = timeline(plan, prof_steps)
+    tl_sum = {"stats": 0.0, "pixel": 0.0, "solve": 0.0}
+    tl_n = {"stats": 0, "pixel": 0, "solve": 0}
+    tl_span = 0.0
+    for spans in tl_runs:
+        for kind, t0, t1 in spans:
+            if t0 is not None:
+                tl_sum[kind] += t1 - t0
+                tl_n[kind] += 1
+        tl_span += max(t1 for _, _, t1 in spans if t1 is not None)
+    nrun = len(tl_runs)
+    in_graph = {kk: tl_sum[kk] / nrun for kk in tl_sum}
+    in_graph["span"] = tl_span / nrun
+    in_graph["gaps"] = in_graph["span"] - (in_graph["stats"] + in_graph["pixel"] +
+                                           in_graph["solve"])
+    in_graph["launches_per_retrieval"] = {kk: tl_n[kk] / nrun for kk in tl_n}
+    in_graph["retrievals"] = nrun
+    in_graph["timing"] = ("device timeline of graph replays of the headline plan: per launch "
+                          "the first CTA's start to the last CTA's end (GPU global timer), "
+                          "summed per kernel kind; us per retrieval")
+    px_tl_s = tl_sum["pixel"] / tl_n["pixel"] * 1e-6
     f32_prof_steps = max(2, f32_steps // 2)
     prof_f32 = profiled(plan_f32, f32_prof_steps)
     px_ms, px_n = prof["pixel"]
@@ -743,7 +781,9 @@ def main():
             "tensor_frac": method_tflops / tc_peak, "tensor_peak_source": tc_src,
             "executed_mma_flop_per_pixel": 2 * 128 * 3 * np_w,
             "executed_mma_tflops": mma_tflops, "executed_mma_frac": mma_tflops / tc_peak,
-            "hbm_gbs": st_gbs, "hbm_frac": st_gbs / hbm}
+            "hbm_gbs": st_gbs, "hbm_frac": st_gbs / hbm,
+            "in_graph_us": in_graph["stats"],
+            "in_graph_hbm_frac": npix * (4 * bands + 1) / (in_graph["stats"] * 1e-6) / 1e9 / hbm}
 
     # --- end to end through the host-buffer entry point (pinned memory)
     cube_h = sc.cube.cpu().pin_memory()
@@ -810,11 +850,17 @@ def main():
                          "traffic": traffic,
                          "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_us": px_avg_s * 1e6, "launches": int(px_n),
-                         "timing": "CUDA events around each launch, direct launches"},
+                         "timing": "CUDA events around each launch, direct launches",
+                         "in_graph": {"avg_launch_us": px_tl_s * 1e6,
+                                      "achieved": alg_bytes / px_tl_s / 1e9,
+                                      "frac": alg_bytes / px_tl_s / 1e9 / hbm,
+                                      "launches": tl_n["pixel"],
+                                      "timing": "device timeline of the graph replays"}},
             "kernels_ms_per_step": {"stats": st_ms / prof_steps, "pixel": px_ms / prof_steps,
                                     "solve": sv_ms / prof_steps,
                                     "timing": "direct launches with CUDA events around every "
                                               "kernel (the headline replays a CUDA graph)"},
+            "kernels_us_in_graph": in_graph,
             "gpu_launches": launches,
             "syrk": syrk,
             "forms": {"bf16split_fused": {"value": value, "ms_per_step": ms_max,

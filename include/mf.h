@@ -253,6 +253,23 @@ mf_status mf_profile(mf_plan_t plan, int32_t enable);
  * arrays).  Synchronises the plan's last stream. */
 mf_status mf_profile_read(mf_plan_t plan, double* ms, int64_t* launches, int32_t n_kinds);
 
+/* Device timeline for roofline reporting of the retrieval as it runs (one
+ * CUDA graph, no events between kernels).  While enabled, thread 0 of every
+ * CTA of every kernel a retrieval launches records the GPU's global timer at
+ * its start and exit into a slot of that launch (two 64-bit atomics per CTA);
+ * the first enable allocates the 64 KB slot buffer (MF_ERR_OOM if it cannot).
+ * Enabling or disabling re-captures the plan's graph on the next call. */
+mf_status mf_timeline(mf_plan_t plan, int32_t enable);
+
+/* Read and clear the timeline of the last retrieval (call it after every
+ * retrieval to be measured).  For launch i < *n (in launch order, at most
+ * cap): start_us[i] / end_us[i] are its first CTA's start and last CTA's end
+ * in microseconds after the retrieval's earliest start (-1 for a launch that
+ * ran no CTA), kind[i] its kernel kind as in mf_profile_read (HOST arrays of
+ * cap entries).  Synchronises the device. */
+mf_status mf_timeline_read(mf_plan_t plan, double* start_us, double* end_us, int32_t* kind,
+                           int32_t cap, int32_t* n);
+
 /* Initial background statistics of every partition -- the mean mu^0 and
  * covariance C^0 of Fig. 1's initialisation, as mf_background returns them
  * after a retrieval -- without allocating any device memory.  The paper has

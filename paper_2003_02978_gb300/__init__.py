@@ -231,6 +231,24 @@ class Plan:
         check(lib().mf_profile_read(self._h, ms, n, 3), "mf_profile_read")
         return {"stats": (ms[0], n[0]), "pixel": (ms[1], n[1]), "solve": (ms[2], n[2])}
 
+    def timeline(self, enable: bool = True):
+        """Device timeline of each retrieval as it runs (graph replay included)."""
+        check(lib().mf_timeline(self._h, int(enable)), "mf_timeline")
+
+    def timeline_read(self, cap: int = 4096):
+        """[(kind, start_us, end_us)] of the last retrieval's launches, kind
+        'stats' | 'pixel' | 'solve', times after its earliest start (None for a
+        launch that ran no CTA); clears the timeline."""
+        t0 = (ctypes.c_double * cap)()
+        t1 = (ctypes.c_double * cap)()
+        kd = (ctypes.c_int32 * cap)()
+        n = ctypes.c_int32(0)
+        check(lib().mf_timeline_read(self._h, t0, t1, kd, int(cap), ctypes.byref(n)),
+              "mf_timeline_read")
+        names = ("stats", "pixel", "solve")
+        return [(names[kd[i]], None if t0[i] < 0 else t0[i], None if t1[i] < 0 else t1[i])
+                for i in range(n.value)]
+
 
 class BatchPlan(Plan):
     """A plan over many flightlines stacked along rows (``line_rows[l]`` rows

@@ -82,7 +82,10 @@ def lib() -> ctypes.CDLL:
     L.mf_retrieve_batched.restype = c_int
     for name, args in (("mf_profile", [c_void_p, c_int32]),
                        ("mf_profile_read", [c_void_p, POINTER(c_double), POINTER(c_int64),
-                                            c_int32])):
+                                            c_int32]),
+                       ("mf_timeline", [c_void_p, c_int32]),
+                       ("mf_timeline_read", [c_void_p, POINTER(c_double), POINTER(c_double),
+                                             POINTER(c_int32), c_int32, POINTER(c_int32)])):
         if hasattr(L, name):
             getattr(L, name).argtypes = args
             getattr(L, name).restype = c_int

@@ -72,10 +72,11 @@ struct mf_plan_s {
     const void* ptr[6];
     int n_iter;
     float eps;
+    bool timeline;
     bool operator==(const GraphKey& o) const {
       for (int i = 0; i < 6; ++i)
         if (ptr[i] != o.ptr[i]) return false;
-      return n_iter == o.n_iter && eps == o.eps;
+      return n_iter == o.n_iter && eps == o.eps && timeline == o.timeline;
     }
   };
   // the last checkpointed forward (mf_retrieve_train), for mf_retrieve_backward
@@ -111,6 +112,12 @@ struct mf_plan_s {
   };
   std::vector<Mark> marks;
   size_t used = 0;
+  // device timeline (mf_timeline): one slot of two words per launch of the
+  // last enqueued retrieval (graph replays reuse the captured slots), and the
+  // kind of each slot's launch
+  bool timeline = false;
+  unsigned long long* tl_dev = nullptr;
+  std::vector<int> tl_kind;
 };
 
 namespace {
@@ -198,40 +205,56 @@ void mark_end(mf_plan_s::Mark* m, cudaStream_t s) {
 
 enum { KIND_STATS = 0, KIND_PIXEL = 1, KIND_SOLVE = 2, KIND_COUNT = 3 };
 
+constexpr size_t kMaxSpans = 4096;  // device timeline slots (launches per retrieval)
+
+// a launch's Params: with the device timeline on, its own slot
+mf::Params span_params(mf_plan_s* pl, const mf::Params& prm, int kind) {
+  mf::Params q = prm;
+  q.tl = nullptr;
+  if (pl->timeline && pl->tl_dev && pl->tl_kind.size() < kMaxSpans) {
+    q.tl = pl->tl_dev;
+    q.tl_slot = (int)pl->tl_kind.size();
+    pl->tl_kind.push_back(kind);
+  }
+  return q;
+}
+
 void stats_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int pass, cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_STATS, s);
   if (pl->d.precision == MF_BF16SPLIT) {
     // persistent: one CTA per SM over the (column, chunk) work items
-    if (mode == mf::STAT_INIT) mf::pilot_launch(s, prm);
+    if (mode == mf::STAT_INIT) mf::pilot_launch(s, span_params(pl, prm, KIND_STATS));
     const int grid = std::min(pl->grid_stats, pl->num_sms);
-    mf::stats_tc_launch(pl->nj, grid, pl->smem_stats, s, pl->map_stats, prm, mode, pass);
+    mf::stats_tc_launch(pl->nj, grid, pl->smem_stats, s, pl->map_stats,
+                        span_params(pl, prm, KIND_STATS), mode, pass);
   } else {
-    if (mode == mf::STAT_INIT) mf::pilot_dirs_launch(s, prm);
-    mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, pl->map_stats, prm, mode, pass);
+    if (mode == mf::STAT_INIT) mf::pilot_dirs_launch(s, span_params(pl, prm, KIND_STATS));
+    mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, pl->map_stats,
+                     span_params(pl, prm, KIND_STATS), mode, pass);
   }
   mark_end(m, s);
 }
 void pixel_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int acc, int pass,
                     cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_PIXEL, s);
-  mf::pixel_launch(pl->nj, pl->grid_pixel, pl->smem_pixel, s, pl->map_pixel, prm, mode, acc,
-                   pass);
+  mf::pixel_launch(pl->nj, pl->grid_pixel, pl->smem_pixel, s, pl->map_pixel,
+                   span_params(pl, prm, KIND_PIXEL), mode, acc, pass);
   mark_end(m, s);
 }
 void solve_init_dispatch(mf_plan_s* pl, const mf::Params& prm, cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_SOLVE, s);
-  mf::solve_init_launch(pl->smem_sinit, s, prm);
+  mf::solve_init_launch(pl->smem_sinit, s, span_params(pl, prm, KIND_SOLVE));
   mark_end(m, s);
 }
 void solve_iter_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int pass,
                          cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_SOLVE, s);
-  mf::solve_iter_launch(pl->smem_siter, s, prm, mode, pass);
+  mf::solve_iter_launch(pl->smem_siter, s, span_params(pl, prm, KIND_SOLVE), mode, pass);
   mark_end(m, s);
 }
 void solve_literal_dispatch(mf_plan_s* pl, const mf::Params& prm, int pass, cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_SOLVE, s);
-  mf::solve_literal_launch(pl->smem_slit, s, prm, pass);
+  mf::solve_literal_launch(pl->smem_slit, s, span_params(pl, prm, KIND_SOLVE), pass);
   mark_end(m, s);
 }
 
@@ -539,6 +562,7 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
     pl->map_cube = cube;
   }
   auto enqueue = [&](cudaStream_t q) {
+    pl->tl_kind.clear();
     cudaMemsetAsync(p.status, 0, (size_t)p.P * sizeof(int), q);
     stats_dispatch(pl, p, mf::STAT_INIT, 0, q);
     solve_init_dispatch(pl, p, q);
@@ -564,7 +588,7 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
     MF_CUDA(cudaGetLastError());
   } else {
     const mf_plan_s::GraphKey key{{cube, k, mask, alpha_init, alpha_out, albedo_out},
-                                  n_iter_max, (float)eps};
+                                  n_iter_max, (float)eps, pl->timeline};
     if (!pl->gexec || !(key == pl->gkey)) {
       if (pl->gexec) {
         MF_CUDA(cudaGraphExecDestroy(pl->gexec));
@@ -644,6 +668,7 @@ void mf_destroy(mf_plan_t pl) {
   if (pl->lines_copied) cudaEventDestroy(pl->lines_copied);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+  cudaFree(pl->tl_dev);
   delete pl;
 }
 
@@ -909,6 +934,58 @@ mf_status mf_profile(mf_plan_t pl, int32_t enable) {
   g_last_error.clear();
   if (!pl) return fail(MF_ERR_INVALID_ARG, "null plan");
   pl->profile = enable != 0;
+  return MF_OK;
+}
+
+mf_status mf_timeline(mf_plan_t pl, int32_t enable) {
+  g_last_error.clear();
+  if (!pl) return fail(MF_ERR_INVALID_ARG, "null plan");
+  if (enable && !pl->tl_dev) {
+    const cudaError_t e = cudaMalloc(&pl->tl_dev, 2 * kMaxSpans * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      pl->tl_dev = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? MF_ERR_OOM : MF_ERR_CUDA,
+                  "timeline buffer: %s", cudaGetErrorString(e));
+    }
+    MF_CUDA(cudaMemset(pl->tl_dev, 0, 2 * kMaxSpans * sizeof(unsigned long long)));
+    MF_CUDA(cudaDeviceSynchronize());
+  }
+  pl->timeline = enable != 0;
+  return MF_OK;
+}
+
+mf_status mf_timeline_read(mf_plan_t pl, double* start_us, double* end_us, int32_t* kind,
+                           int32_t cap, int32_t* n) {
+  g_last_error.clear();
+  if (!pl || !start_us || !end_us || !kind || !n || cap < 0)
+    return fail(MF_ERR_INVALID_ARG, "bad argument");
+  *n = 0;
+  if (!pl->tl_dev) return MF_OK;
+  if (pl->last_stream) MF_CUDA(cudaStreamSynchronize(pl->last_stream));
+  const size_t m = pl->tl_kind.size();
+  std::vector<unsigned long long> w(2 * std::max<size_t>(m, 1));
+  if (m) MF_CUDA(cudaMemcpy(w.data(), pl->tl_dev, 2 * m * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost));
+  // cleared for the next retrieval, whatever stream it runs on
+  MF_CUDA(cudaMemset(pl->tl_dev, 0, 2 * kMaxSpans * sizeof(unsigned long long)));
+  MF_CUDA(cudaDeviceSynchronize());
+  // times relative to the earliest recorded start; a slot whose launch
+  // recorded nothing (no CTA ran, e.g. a line with its iterations done) is
+  // reported with start = end = -1
+  unsigned long long t0 = ~0ull;
+  for (size_t i = 0; i < m; ++i)
+    if (w[2 * i + 1]) t0 = std::min(t0, ~w[2 * i]);
+  const int32_t out = (int32_t)std::min<size_t>(m, (size_t)cap);
+  for (int32_t i = 0; i < out; ++i) {
+    kind[i] = pl->tl_kind[i];
+    if (w[2 * i + 1]) {
+      start_us[i] = (double)(~w[2 * i] - t0) * 1e-3;
+      end_us[i] = (double)(w[2 * i + 1] - t0) * 1e-3;
+    } else {
+      start_us[i] = end_us[i] = -1.0;
+    }
+  }
+  *n = out;
   return MF_OK;
 }
 

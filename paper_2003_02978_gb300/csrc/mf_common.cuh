@@ -127,6 +127,33 @@ struct Params {
   float2* ck_vec;       // (P, n + 1, 4, B)
   double* ck_sc;        // (P, n + 1, 4)
   int ck_stages;        // n + 1
+  // device timeline (mf_timeline; null: off): two words per launch, this
+  // launch's at tl + 2 tl_slot
+  unsigned long long* tl;
+  int tl_slot;
+};
+
+// Device timeline of a launch (mf_timeline).  When p.tl is set, thread 0 of
+// every CTA folds %globaltimer (ns) at its start into slot[0] and at its exit
+// into slot[1], both by atomicMax on zero-initialised words: slot[0] keeps
+// the largest bitwise complement, i.e. the earliest start, slot[1] the
+// latest exit, so the slot spans the launch from its first CTA's start to
+// its last CTA's end.  One instance at the top of a kernel covers every
+// return path.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+struct LaunchSpan {
+  unsigned long long* s;
+  __device__ explicit LaunchSpan(const Params& p)
+      : s(p.tl && threadIdx.x == 0 ? p.tl + 2 * (size_t)p.tl_slot : nullptr) {
+    if (s) atomicMax(s, ~globaltimer_ns());
+  }
+  __device__ ~LaunchSpan() {
+    if (s) atomicMax(s + 1, globaltimer_ns());
+  }
 };
 
 enum : int { CKV_MU = 0, CKV_T, CKV_V, CKV_G };

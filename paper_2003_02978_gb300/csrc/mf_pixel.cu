@@ -61,6 +61,7 @@ template <int NJ>
 __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     pixel_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode, int accumulate,
                  int pass) {
+  const LaunchSpan span(p);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_abort;
   __shared__ int s_failed[kTileCols];

@@ -276,6 +276,7 @@ size_t solve_literal_smem_bytes(int B, int BA) {
 }
 
 __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
+  const LaunchSpan span(p);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df red[kWarps];
   const int part = blockIdx.x;
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
 }
 
 __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int mode, int pass) {
+  const LaunchSpan span(p);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df s_y[3];
   __shared__ int s_bad;
@@ -662,6 +664,7 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
 }
 
 __global__ void __launch_bounds__(kThreads, 4) solve_literal_kernel(Params p, int pass) {
+  const LaunchSpan span(p);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df red[kWarps];
   const int part = blockIdx.x;

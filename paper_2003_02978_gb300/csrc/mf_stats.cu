@@ -75,6 +75,7 @@ size_t stats_smem_bytes(int B, int K) { return stat_layout(B, K).total + 128; }
 // Any directions give the same moments in exact arithmetic: these keep what
 // is accumulated in float32 small.  One warp per partition.
 __global__ void pilot_dirs_kernel(Params p) {
+  const LaunchSpan span(p);
   const int part = blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (part >= p.P) return;
@@ -184,6 +185,7 @@ static_assert(kMaxDirs + 2 <= 12, "a pixel's coefficients fill at most three flo
 template <int NJ>
 __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__ CUtensorMap map,
                                                          Params p, int mode, int pass) {
+  const LaunchSpan span(p);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(16) float s_dir[kMaxDirs * kMaxB];   // q_k, k < K
   __shared__ __align__(16) float s_mu0f[kMaxB];             // literal: mu^0 for r_i

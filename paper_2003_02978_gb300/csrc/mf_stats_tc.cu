@@ -136,6 +136,7 @@ bool stats_tc_supported(int B) {
 // partition.
 constexpr int kPilot = 8;
 __global__ void pilot_kernel(Params p) {
+  const LaunchSpan span(p);
   const int part = blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (part >= p.P) return;
@@ -210,6 +211,7 @@ __device__ __forceinline__ void conv_bar() {
 template <int NJ>
 __global__ void __launch_bounds__(kTcThreads, 1)
     stats_tc_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode, int pass) {
+  const LaunchSpan span(p);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int s_abort;
 
