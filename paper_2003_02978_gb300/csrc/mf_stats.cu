@@ -182,6 +182,38 @@ void pilot_dirs_launch(cudaStream_t s, const Params& p) {
 
 static_assert(kMaxDirs + 2 <= 12, "a pixel's coefficients fill at most three float4 groups");
 
+// Thread slot t -> 4 x 4 block (bi, bj), bi <= bj, of the upper triangle of
+// nb x nb blocks, enumerated by groups of four block rows, each group column
+// by column with the rows of a column fastest (column c of a group of h rows
+// holds min(h, c + 1) blocks).  A warp's 32 consecutive slots then cover
+// about 4 block rows x 8 block columns, so that per pixel its two float4 loads
+// touch 4 + 8 distinct addresses; in row-major order they touch up to 32.
+__device__ inline void tile_decode(int t, int nb, int& bi, int& bj) {
+  for (int r0 = 0; r0 < nb; r0 += 4) {
+    const int h = min(4, nb - r0), ncol = nb - r0;
+    const int tri = h * (h + 1) / 2;  // the first h columns
+    const int cnt = tri + (ncol - h) * h;
+    if (t < cnt) {
+      int c = 0, r;
+      if (t < tri) {
+        while (t >= c + 1) {
+          t -= c + 1;
+          ++c;
+        }
+        r = t;
+      } else {
+        c = h + (t - tri) / h;
+        r = (t - tri) % h;
+      }
+      bi = r0 + r;
+      bj = r0 + c;
+      return;
+    }
+    t -= cnt;
+  }
+  bi = bj = 0;  // t >= nb (nb + 1) / 2: not reached
+}
+
 template <int NJ>
 __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__ CUtensorMap map,
                                                          Params p, int mode, int pass) {
@@ -246,9 +278,10 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
   const float inv_mu2 = mode == STAT_LITERAL ? p.pscal[(size_t)part * PS_N + PS_INVMU2] : 0.f;
   const bool albedo = (p.flags & MF_ALBEDO) != 0;
 
-  // ---- SYRK ownership: 4x4 blocks of the upper triangle, blocks tid,
-  // tid + 256, ...; double-float accumulators in shared memory, block-major
-  // with the 32 floats (16 hi, 16 lo) of a block strided by nblk
+  // ---- SYRK ownership: 4x4 blocks of the upper triangle, slots tid,
+  // tid + 256, ... (tile_decode); double-float accumulators in shared
+  // memory, slot-major with the 32 floats (16 hi, 16 lo) of a slot strided by
+  // nblk
   const int nb = BA / 4;
   const int nblk = nb * (nb + 1) / 2;
   const int bcoef = B / 4;  // first block of the coefficients
@@ -314,7 +347,7 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
     // phase B: augmented SYRK over the 128 pixels of the stage
     for (int blk = tid; blk < nblk; blk += kThreads) {
       int bi, bj;
-      block_of(blk, nb, bi, bj);
+      tile_decode(blk, nb, bi, bj);
       // row pointers and strides: the coefficient blocks live in coef[]
       const float* cbase = reinterpret_cast<const float*>(coef);
       const float* pa = (bi >= bcoef) ? cbase + 4 * (bi - bcoef) : stage[sb] + 4 * bi;
@@ -377,12 +410,17 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
     return;
   }
 
-  // ---- publish this CTA's moments (double-float pairs)
+  // ---- publish this CTA's moments (double-float pairs), blocks in
+  // row-major order of the upper triangle: block (bi, bj) at
+  // bi nb - bi (bi - 1) / 2 + bj - bi
   const int K1E = k1_entries(BA);
   float2* dst = p.k1part + (size_t)it.unit * K1E;
   for (int q = tid; q < nblk * 16; q += kThreads) {
-    const int blk = q >> 4, w = q & 15;
-    dst[q] = make_float2(accs[w * nblk + blk], accs[(16 + w) * nblk + blk]);
+    const int slot = q >> 4, w = q & 15;
+    int bi, bj;
+    tile_decode(slot, nb, bi, bj);
+    const int blk = bi * nb - bi * (bi - 1) / 2 + (bj - bi);
+    dst[(size_t)blk * 16 + w] = make_float2(accs[w * nblk + slot], accs[(16 + w) * nblk + slot]);
   }
 }
 
