@@ -378,8 +378,9 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   p.fault_notspd = fault_s == "notspd";
   p.test_wait = fault_s == "timeout" ? 2000 : 0;
   {
-    // the share of the cube that a pixel pass leaves in L2 for the next one:
-    // about 3/4 of the L2 (the rest holds the pass's writes and moments)
+    // the share of the cube that a backward pixel pass leaves in L2 for the
+    // next one: about 3/4 of the L2 (the rest holds the pass's writes and
+    // moments)
     int dev = 0, l2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);

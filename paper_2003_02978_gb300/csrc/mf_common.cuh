@@ -81,8 +81,9 @@ struct Params {
   int n_lines, n_items, n_blocks;  // lines; statistics items; pixel CTAs
   uint32_t flags;
   float eps;
-  float l2_keep;          // pixel passes: fraction of each CTA's stages read last that
-                          // are kept in L2 for the next pass (it walks the rows back)
+  float l2_keep;          // backward pixel passes: fraction of each CTA's stages read
+                          // last that are kept in L2 for the next pass (it walks the
+                          // rows back)
   int force_direct;       // test hook (MF_FORCE_DIRECT=1 at plan creation): every fused
                           // iteration takes the direct factorisation of C^k
   long long test_wait;    // fault hook (MF_FAULT=timeout): > 0 makes every pixel CTA of

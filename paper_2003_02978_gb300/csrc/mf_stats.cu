@@ -256,7 +256,9 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
     prefetch_tmap(&map);
     for (int s = 0; s < 2 && s < nst; ++s) {
       mbar_arrive_expect_tx(&full[s], box_bytes);
-      tma_load_3d(stage[s], &map, p.band_lo, c, r_beg + s * kStatRows, &full[s]);
+      // evict-first: the moment partials the solves read next stay in L2
+      tma_load_3d_hint(stage[s], &map, p.band_lo, c, r_beg + s * kStatRows, &full[s],
+                       l2_policy_evict_first());
       ++issued[s];
     }
   }
@@ -396,7 +398,8 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__
     if (tid == 0 && i + 2 < nst) {
       fence_proxy_async_smem();  // phase A wrote this buffer through the generic proxy
       mbar_arrive_expect_tx(&full[sb], box_bytes);
-      tma_load_3d(stage[sb], &map, p.band_lo, c, r_beg + (i + 2) * kStatRows, &full[sb]);
+      tma_load_3d_hint(stage[sb], &map, p.band_lo, c, r_beg + (i + 2) * kStatRows, &full[sb],
+                       l2_policy_evict_first());
       ++issued[sb];
     }
   }

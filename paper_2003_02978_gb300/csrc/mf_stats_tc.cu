@@ -293,7 +293,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
           }
           mbar_arrive_expect_tx(&fp_full[fb], box_bytes);
-          tma_load_3d(stage(fb), &map, p.band_lo, it.c, it.r_beg + s * kTcRows, &fp_full[fb]);
+          // evict-first: the moment partials the initial solve reads next
+          // stay in L2
+          tma_load_3d_hint(stage(fb), &map, p.band_lo, it.c, it.r_beg + s * kTcRows, &fp_full[fb],
+                           l2_policy_evict_first());
           ++issued[fb];
         }
       }
