@@ -333,54 +333,81 @@ __host__ __device__ inline int linv_ld(int B) { return B + 1; }
 // shared memory (B rows of linv_ld(B) double-floats, zeros above the
 // diagonal, as stored by the initial solve).  Pair q comes interleaved,
 // UP[q][j] = (a_j.hi, b_j.hi, a_j.lo, b_j.lo); YP[q] is scratch of the same
-// form; the results go to Z[2q] (a) and Z[2q + 1] (b).  Y = X U by two
-// lanes per (pair, row), then Z = X^T Y by two lanes per (pair, column),
-// each lane taking every other term, with packed compensated sums; the two
-// partial sums of a lane pair are merged by a shuffle.
+// form; the results go to Z[2q] (a) and Z[2q + 1] (b).  Y = X U row by row,
+// then Z = X^T Y column by column, with packed compensated sums.  A row of
+// i + 1 terms (a column of B - i) is split over 4 lanes, each taking every
+// fourth term, or over 2 lanes for the first r2 rows (the shortest), so that
+// one pass of the block covers all B rows: 4 (B - r2) + 2 r2 <= kThreads.
+// The 4-lane rows fill whole warps first, so that no row's lanes straddle a
+// warp; the lanes' partial sums are merged by shuffles, always in the same
+// order.
+__device__ __forceinline__ void apply_lanes(int B, int tid, int& row, int& sub, int& nl) {
+  const int r2 = max(0, 2 * B - kThreads / 2);  // rows on 2 lanes: 0 .. r2 - 1
+  const int l4 = 4 * (B - r2);                  // lanes of the 4-lane rows
+  if (tid < l4) {
+    row = r2 + (tid >> 2);
+    sub = tid & 3;
+    nl = 4;
+  } else if (tid < l4 + 2 * r2) {
+    row = (tid - l4) >> 1;
+    sub = tid & 1;
+    nl = 2;
+  } else {
+    row = -1;
+    sub = 0;
+    nl = 2;
+  }
+}
+__device__ __forceinline__ void merge_apply_lanes(Dot2x2& d, int nl) {
+  d.merge_lane_pair();
+  // every lane takes part in the shuffles; only the 4-lane rows merge
+  const float2 s2 = make_float2(__shfl_xor_sync(0xffffffffu, d.s.x, 2),
+                                __shfl_xor_sync(0xffffffffu, d.s.y, 2));
+  const float2 c2 = make_float2(__shfl_xor_sync(0xffffffffu, d.c.x, 2),
+                                __shfl_xor_sync(0xffffffffu, d.c.y, 2));
+  if (nl == 4) d.merge(s2, c2);
+}
 template <int NP>
 __device__ void c0inv_apply(const df* X, int B, const float4* const* UP, float4* const* YP,
                             df* const* Z) {
-  const int tid = threadIdx.x, ld = linv_ld(B), h = tid & 1;
-  const int total = 2 * NP * B;
-  for (int base = 0; base < total; base += kThreads) {
-    const int w = base + tid;
-    const bool act = w < total;
-    const int o = act ? w >> 1 : 0;
-    const int q = o / B, i = o - q * B;
+  static_assert(kThreads >= 2 * kMaxB, "two lanes per row at the widest window");
+  const int tid = threadIdx.x, ld = linv_ld(B);
+  int r, sub, nl;
+  apply_lanes(B, tid, r, sub, nl);
+  for (int q = 0; q < NP; ++q) {
     Dot2x2 d;
-    if (act) {
+    if (r >= 0) {
+      const int i = r;
       const df* row = X + (size_t)i * ld;
       const float4* u = UP[q];
 #pragma unroll 4
-      for (int j = h; j <= i; j += 2) {
+      for (int j = sub; j <= i; j += nl) {
         const float4 uu = u[j];
         d.add(row[j], make_float2(uu.x, uu.y), make_float2(uu.z, uu.w));
       }
     }
-    d.merge_lane_pair();
-    if (act && h == 0) {
+    merge_apply_lanes(d, nl);
+    if (r >= 0 && sub == 0) {
       float2 rh, rl;
       d.result(rh, rl);
-      YP[q][i] = make_float4(rh.x, rh.y, rl.x, rl.y);
+      YP[q][r] = make_float4(rh.x, rh.y, rl.x, rl.y);
     }
   }
   __syncthreads();
-  for (int base = 0; base < total; base += kThreads) {
-    const int w = base + tid;
-    const bool act = w < total;
-    const int o = act ? w >> 1 : 0;
-    const int q = o / B, j = o - q * B;
+  for (int q = 0; q < NP; ++q) {
     Dot2x2 d;
-    if (act) {
+    // column j = B - 1 - r holds B - j = r + 1 terms, like row r above
+    const int j = B - 1 - r;
+    if (r >= 0) {
       const float4* y = YP[q];
 #pragma unroll 4
-      for (int i = j + h; i < B; i += 2) {
+      for (int i = j + sub; i < B; i += nl) {
         const float4 yy = y[i];
         d.add(X[(size_t)i * ld + j], make_float2(yy.x, yy.y), make_float2(yy.z, yy.w));
       }
     }
-    d.merge_lane_pair();
-    if (act && h == 0) {
+    merge_apply_lanes(d, nl);
+    if (r >= 0 && sub == 0) {
       float2 rh, rl;
       d.result(rh, rl);
       Z[2 * q][j] = df{rh.x, rl.x};
