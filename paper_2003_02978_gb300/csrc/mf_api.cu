@@ -90,6 +90,9 @@ struct mf_plan_s {
     double eps = 0.0;
   } train;
   bool use_graph = true;
+  // launch every kernel but a retrieval's first with programmatic stream
+  // serialisation (MF_PDL=0 at plan creation: off)
+  bool pdl = true;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   GraphKey gkey{};
@@ -208,9 +211,12 @@ enum { KIND_STATS = 0, KIND_PIXEL = 1, KIND_SOLVE = 2, KIND_COUNT = 3 };
 
 constexpr size_t kMaxSpans = 4096;  // device timeline slots (launches per retrieval)
 
-// a launch's Params: with the device timeline on, its own slot
-mf::Params span_params(mf_plan_s* pl, const mf::Params& prm, int kind) {
+// a launch's Params: with the device timeline on, its own slot; `first`:
+// the retrieval's first kernel, which follows a memset, not a kernel, and is
+// launched without the programmatic attribute
+mf::Params span_params(mf_plan_s* pl, const mf::Params& prm, int kind, bool first = false) {
   mf::Params q = prm;
+  q.pdl = pl->pdl && !first;
   q.tl = nullptr;
   if (pl->timeline && pl->tl_dev && pl->tl_kind.size() < kMaxSpans) {
     q.tl = pl->tl_dev;
@@ -224,12 +230,12 @@ void stats_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int pass, cu
   mf_plan_s::Mark* m = mark_begin(pl, KIND_STATS, s);
   if (pl->d.precision == MF_BF16SPLIT) {
     // persistent: one CTA per SM over the (column, chunk) work items
-    if (mode == mf::STAT_INIT) mf::pilot_launch(s, span_params(pl, prm, KIND_STATS));
+    if (mode == mf::STAT_INIT) mf::pilot_launch(s, span_params(pl, prm, KIND_STATS, true));
     const int grid = std::min(pl->grid_stats, pl->num_sms);
     mf::stats_tc_launch(pl->nj, grid, pl->smem_stats, s, pl->map_stats,
                         span_params(pl, prm, KIND_STATS), mode, pass);
   } else {
-    if (mode == mf::STAT_INIT) mf::pilot_dirs_launch(s, span_params(pl, prm, KIND_STATS));
+    if (mode == mf::STAT_INIT) mf::pilot_dirs_launch(s, span_params(pl, prm, KIND_STATS, true));
     mf::stats_launch(pl->nj, pl->grid_stats, pl->smem_stats, s, pl->map_stats,
                      span_params(pl, prm, KIND_STATS), mode, pass);
   }
@@ -354,6 +360,7 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   p.n_lines = n_lines;
   pl->nj = nj_bucket(p.B4);
   pl->use_graph = env_int("MF_GRAPH", 1) != 0;
+  pl->pdl = env_int("MF_PDL", 1) != 0;
   if (tune && tune->use_graph < 0) pl->use_graph = false;
 
   cudaError_t e = cudaGetDevice(&pl->device);

@@ -132,7 +132,41 @@ struct Params {
   // launch's at tl + 2 tl_slot
   unsigned long long* tl;
   int tl_slot;
+  // launch with programmatic stream serialisation (see pdl_wait)
+  int pdl;
 };
+
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may start while the kernel before it in
+// the stream still runs: up to pdl_wait() it may only touch data no running
+// kernel writes or reads (the cube, the mask, the plan's line table, and the
+// outputs of kernels two or more launches back); pdl_wait() returns once
+// the previous kernel has completed and its writes are visible.  Every
+// kernel signals its dependents (pdl_trigger) only after its own wait, so at
+// most two kernels overlap and everything two launches back is complete.
+// Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// launch `kernel` on `s`, with the programmatic stream-serialisation
+// attribute when `pdl` is set
+template <typename... KArgs, typename... Args>
+inline void launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t s, bool pdl, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
 
 // Device timeline of a launch (mf_timeline).  When p.tl is set, thread 0 of
 // every CTA folds %globaltimer (ns) at its start into slot[0] and at its exit

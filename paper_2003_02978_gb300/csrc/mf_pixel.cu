@@ -51,7 +51,11 @@ __host__ __device__ inline PixSmem pix_layout(int B, int BP) {
 }  // namespace
 
 // two CTAs per SM (registers capped at 128 per thread) up to 72 bands; one
-// above, where the band registers would spill
+// above, where the band registers would spill.  The kernel is launched
+// without the programmatic attribute (measured: a pixel pass whose CTAs were
+// placed early, as the solve's CTAs left, ran 4 us slower per launch); it
+// still signals its dependents after its (then no-op) wait, so that the next
+// solve's CTAs start their copies as the pass's CTAs finish.
 constexpr int pix_ctas_per_sm(int nj) { return nj <= 9 ? 2 : 1; }
 
 size_t pixel_smem_bytes(int B, int nj) { return pix_layout(B, 8 * nj).total + 128; }
@@ -61,7 +65,6 @@ template <int NJ>
 __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     pixel_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode, int accumulate,
                  int pass) {
-  const LaunchSpan span(p);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_abort;
   __shared__ int s_failed[kTileCols];
@@ -124,6 +127,13 @@ __global__ void __launch_bounds__(kPixThreads, pix_ctas_per_sm(NJ))
     prefetch_tmap(&map);
     for (int i = 0; i < kPixStages && i < nst; ++i) load(i, i);
   }
+  // the first stages of the cube are on their way; what follows reads the
+  // previous kernel's outputs (the solve's parameters and status) and
+  // writes alpha and the moments it may still read (a no-op wait, as this
+  // kernel is launched in stream order)
+  pdl_wait();
+  pdl_trigger();
+  const LaunchSpan span(p);
   // per-column parameters of the current pass
   for (int idx = tid; idx < kTileCols * BP; idx += kPixThreads) {
     const int cc = idx / BP, b = idx % BP;
@@ -358,7 +368,8 @@ void pixel_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorM
                   const Params& p, int mode, int accumulate, int pass) {
 #define MF_CASE(NJ)                                                        \
   case NJ:                                                                 \
-    pixel_kernel<NJ><<<grid, kPixThreads, smem, s>>>(map, p, mode, accumulate, pass); \
+    launch_kernel(pixel_kernel<NJ>, grid, kPixThreads, smem, s, false, map, p, mode, accumulate, \
+                  pass);                                                 \
     return;
   switch (nj) { MF_NJ_CASES(MF_CASE) }
 #undef MF_CASE

@@ -276,6 +276,8 @@ size_t solve_literal_smem_bytes(int B, int BA) {
 }
 
 __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
+  pdl_wait();
+  pdl_trigger();
   const LaunchSpan span(p);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df red[kWarps];
@@ -372,7 +374,6 @@ __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
 }
 
 __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int mode, int pass) {
-  const LaunchSpan span(p);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df s_y[3];
   __shared__ int s_bad;
@@ -381,7 +382,6 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
   const int tid = threadIdx.x;
   const int B = p.B;
   const size_t pb = (size_t)part * B;
-  if (p.status[part] != MF_OK) return;
   if (pass > p.lines[part_line(p, part)].n_iter) return;  // the line's iterations are done
   // L^{-1} (B rows of linv_ld(B) double-floats), later the direct path's
   // B x B matrix
@@ -425,6 +425,16 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
     mbar_fence_init();
     mbar_arrive_expect_tx(&s_xbar, bytes);
     bulk_load(X, p.Linv + (size_t)part * n, bytes, &s_xbar);
+  }
+  // all of the above comes from kernels two or more launches back; the
+  // moments, the status and every write below wait for the pixel pass
+  pdl_wait();
+  pdl_trigger();
+  const LaunchSpan span(p);
+  if (p.status[part] != MF_OK) {
+    // a failed partition: its copy lands before the CTA leaves
+    if (solve && tid == 0) mbar_wait(&s_xbar, 0);
+    return;
   }
 
   const int K3E = k3_entries(B);
@@ -664,6 +674,8 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
 }
 
 __global__ void __launch_bounds__(kThreads, 4) solve_literal_kernel(Params p, int pass) {
+  pdl_wait();
+  pdl_trigger();
   const LaunchSpan span(p);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ df red[kWarps];
@@ -804,13 +816,13 @@ void energy_final_launch(cudaStream_t s, const Params& p, int k) {
 }
 
 void solve_init_launch(size_t smem, cudaStream_t s, const Params& p) {
-  solve_init_kernel<<<p.P, kThreads, smem, s>>>(p);
+  launch_kernel(solve_init_kernel, p.P, kThreads, smem, s, p.pdl != 0, p);
 }
 void solve_iter_launch(size_t smem, cudaStream_t s, const Params& p, int mode, int pass) {
-  solve_iter_kernel<<<p.P, kThreads, smem, s>>>(p, mode, pass);
+  launch_kernel(solve_iter_kernel, p.P, kThreads, smem, s, p.pdl != 0, p, mode, pass);
 }
 void solve_literal_launch(size_t smem, cudaStream_t s, const Params& p, int pass) {
-  solve_literal_kernel<<<p.P, kThreads, smem, s>>>(p, pass);
+  launch_kernel(solve_literal_kernel, p.P, kThreads, smem, s, p.pdl != 0, p, pass);
 }
 
 }  // namespace mf

@@ -217,6 +217,8 @@ __device__ inline void tile_decode(int t, int nb, int& bi, int& bj) {
 template <int NJ>
 __global__ void __launch_bounds__(kThreads) stats_kernel(const __grid_constant__ CUtensorMap map,
                                                          Params p, int mode, int pass) {
+  pdl_wait();
+  pdl_trigger();
   const LaunchSpan span(p);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(16) float s_dir[kMaxDirs * kMaxB];   // q_k, k < K
@@ -443,7 +445,7 @@ void stats_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorM
                   const Params& p, int mode, int pass) {
 #define MF_CASE(NJ)                                                     \
   case NJ:                                                              \
-    stats_kernel<NJ><<<grid, kThreads, smem, s>>>(map, p, mode, pass);  \
+    launch_kernel(stats_kernel<NJ>, grid, kThreads, smem, s, p.pdl != 0, map, p, mode, pass); \
     return;
   switch (nj) { MF_NJ_CASES(MF_CASE) }
 #undef MF_CASE

@@ -211,7 +211,6 @@ __device__ __forceinline__ void conv_bar() {
 template <int NJ>
 __global__ void __launch_bounds__(kTcThreads, 1)
     stats_tc_kernel(const __grid_constant__ CUtensorMap map, Params p, int mode, int pass) {
-  const LaunchSpan span(p);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int s_abort;
 
@@ -411,6 +410,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else {
     // ---------------- converters (warps 0-7)
+    // the reference directions (and in the literal schedule alpha) come from
+    // the previous kernels: wait for the last of them.  The producer's copies
+    // of the cube, the MMAs and the epilogue need no wait.
+    pdl_wait();
+    pdl_trigger();
+    const LaunchSpan span(p);
     const int e = lane & 1;
     const int slot = warp * 16 + (lane >> 1);  // pixel = K index within a stage
     const bool albedo = (p.flags & MF_ALBEDO) != 0;
@@ -615,7 +620,8 @@ void stats_tc_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtens
                      const Params& p, int mode, int pass) {
 #define MF_CASE(NJ)                                                             \
   case NJ:                                                                      \
-    stats_tc_kernel<NJ><<<grid, kTcThreads, smem, s>>>(map, p, mode, pass);     \
+    launch_kernel(stats_tc_kernel<NJ>, grid, kTcThreads, smem, s, p.pdl != 0, map, p, mode, \
+                  pass);                                                          \
     return;
   switch (nj) { MF_NJ_CASES(MF_CASE) }
 #undef MF_CASE
