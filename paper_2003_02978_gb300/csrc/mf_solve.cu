@@ -90,32 +90,35 @@ __device__ void reduce_k1(const Params& p, int part, const DfMat& A) {
   constexpr int kU = 8;
   if (p.k1_colmajor) {
     // units of Q (column-major floats, BA x BA, BA a multiple of 4): R = the
-    // sum of the units' Q into A, two entries per load; then G = R + R^T in
-    // place
+    // sum of the units' Q into A, two entries per load, four entries x four
+    // units = 16 loads in flight per thread; then G = R + R^T in place
+    constexpr int kH = 4, kUq = 4;
     const float2* Q0 = P0;
     const size_t ustride = K1E;  // float2 per unit
     const int BB = BA * BA, BB2 = BB / 2;
-    for (int q0 = threadIdx.x; q0 < BB2; q0 += 2 * kThreads) {
-      df sx[2] = {df{0.f, 0.f}, df{0.f, 0.f}}, sy[2] = {df{0.f, 0.f}, df{0.f, 0.f}};
-      for (int u0 = 0; u0 < nunits; u0 += kU) {
-        float2 v[2][kU];
+    for (int q0 = threadIdx.x; q0 < BB2; q0 += kH * kThreads) {
+      df sx[kH], sy[kH];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < kH; ++h) sx[h] = sy[h] = df{0.f, 0.f};
+      for (int u0 = 0; u0 < nunits; u0 += kUq) {
+        float2 v[kH][kUq];
 #pragma unroll
-          for (int k = 0; k < kU; ++k) {
+        for (int h = 0; h < kH; ++h)
+#pragma unroll
+          for (int k = 0; k < kUq; ++k) {
             const int q = q0 + h * kThreads, u = u0 + k;
             v[h][k] = (q < BB2 && u < nunits) ? Q0[(size_t)u * ustride + q] : make_float2(0.f, 0.f);
           }
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < kH; ++h)
 #pragma unroll
-          for (int k = 0; k < kU; ++k) {
+          for (int k = 0; k < kUq; ++k) {
             sx[h] = df_addf(sx[h], v[h][k].x);
             sy[h] = df_addf(sy[h], v[h][k].y);
           }
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < kH; ++h) {
         const int q = 2 * (q0 + h * kThreads);  // Q_mj at j BA + m
         if (q < BB) {
           A.set(q % BA, q / BA, sx[h]);
