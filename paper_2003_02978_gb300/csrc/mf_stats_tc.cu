@@ -136,6 +136,9 @@ bool stats_tc_supported(int B) {
 // partition.
 constexpr int kPilot = 8;
 __global__ void pilot_kernel(Params p) {
+  // a retrieval's first kernel: the statistics kernel after it may start its
+  // cube copies at once (its converters wait before reading the reference)
+  pdl_trigger();
   const LaunchSpan span(p);
   const int part = blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
