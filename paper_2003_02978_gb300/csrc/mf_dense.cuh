@@ -304,43 +304,6 @@ __device__ inline bool chol_inv_df(const DfMat& A, int n, df* invd) {
   return true;
 }
 
-// z = C^{-1} b = X^T (X b), X from chol_inv_df (strict lower triangle of
-// A, diagonal invd); y is scratch; neither may alias b.  Thread per row,
-// compensated sums.
-__device__ inline void xtx_apply_df(const DfMat& A, int n, const df* invd, const df* b, df* y, df* z) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < n; i += kThreads) {
-    Dot2 d;
-    d.add(invd[i], b[i]);
-    for (int j = 0; j < i; ++j) d.add(A.get(i, j), b[j]);
-    y[i] = d.result();
-  }
-  __syncthreads();
-  for (int j = tid; j < n; j += kThreads) {
-    Dot2 d;
-    d.add(invd[j], y[j]);
-    for (int i = j + 1; i < n; ++i) d.add(A.get(i, j), y[i]);
-    z[j] = d.result();
-  }
-  __syncthreads();
-}
-
-// row stride (double-floats) of the stored inverse factor: B + 1 keeps the
-// row walk and the column walk of c0inv_apply free of bank conflicts
-__host__ __device__ inline int linv_ld(int B) { return B + 1; }
-
-// Z = C^{-1} [a, b] for NP pairs of vectors, with X = L^{-1} row-major in
-// shared memory (B rows of linv_ld(B) double-floats, zeros above the
-// diagonal, as stored by the initial solve).  Pair q comes interleaved,
-// UP[q][j] = (a_j.hi, b_j.hi, a_j.lo, b_j.lo); YP[q] is scratch of the same
-// form; the results go to Z[2q] (a) and Z[2q + 1] (b).  Y = X U row by row,
-// then Z = X^T Y column by column, with packed compensated sums.  A row of
-// i + 1 terms (a column of B - i) is split over 4 lanes, each taking every
-// fourth term, or over 2 lanes for the first r2 rows (the shortest), so that
-// one pass of the block covers all B rows: 4 (B - r2) + 2 r2 <= kThreads.
-// The 4-lane rows fill whole warps first, so that no row's lanes straddle a
-// warp; the lanes' partial sums are merged by shuffles, always in the same
-// order.
 __device__ __forceinline__ void apply_lanes(int B, int tid, int& row, int& sub, int& nl) {
   const int r2 = max(0, 2 * B - kThreads / 2);  // rows on 2 lanes: 0 .. r2 - 1
   const int l4 = 4 * (B - r2);                  // lanes of the 4-lane rows
@@ -367,6 +330,62 @@ __device__ __forceinline__ void merge_apply_lanes(Dot2x2& d, int nl) {
                                 __shfl_xor_sync(0xffffffffu, d.c.y, 2));
   if (nl == 4) d.merge(s2, c2);
 }
+// a scalar Dot2 partial sum merged with that of the lane whose index differs
+// in bit `o` (every lane calls; `apply`: this lane takes the merge)
+__device__ __forceinline__ void dot2_merge_xor(Dot2& d, int o, bool apply) {
+  const float s2 = __shfl_xor_sync(0xffffffffu, d.s, o);
+  const float c2 = __shfl_xor_sync(0xffffffffu, d.c, o);
+  if (apply) {
+    const df t = two_sum(d.s, s2);
+    d.s = t.hi;
+    d.c = __fadd_rn(d.c, __fadd_rn(c2, t.lo));
+  }
+}
+
+// z = C^{-1} b = X^T (X b), X from chol_inv_df (strict lower triangle of
+// A, diagonal invd); y is scratch; neither may alias b.  Rows (then
+// columns) on 4 or 2 lanes as in apply_lanes, compensated sums.
+__device__ inline void xtx_apply_df(const DfMat& A, int n, const df* invd, const df* b, df* y, df* z) {
+  int r, sub, nl;
+  apply_lanes(n, threadIdx.x, r, sub, nl);
+  {
+    Dot2 d;
+    if (r >= 0)
+      for (int j = sub; j <= r; j += nl) d.add(j == r ? invd[r] : A.get(r, j), b[j]);
+    dot2_merge_xor(d, 1, true);
+    dot2_merge_xor(d, 2, nl == 4);
+    if (r >= 0 && sub == 0) y[r] = d.result();
+  }
+  __syncthreads();
+  {
+    // column j = n - 1 - r holds n - j = r + 1 terms, like row r above
+    const int j = n - 1 - r;
+    Dot2 d;
+    if (r >= 0)
+      for (int i = j + sub; i < n; i += nl) d.add(i == j ? invd[j] : A.get(i, j), y[i]);
+    dot2_merge_xor(d, 1, true);
+    dot2_merge_xor(d, 2, nl == 4);
+    if (r >= 0 && sub == 0) z[j] = d.result();
+  }
+  __syncthreads();
+}
+
+// row stride (double-floats) of the stored inverse factor: B + 1 keeps the
+// row walk and the column walk of c0inv_apply free of bank conflicts
+__host__ __device__ inline int linv_ld(int B) { return B + 1; }
+
+// Z = C^{-1} [a, b] for NP pairs of vectors, with X = L^{-1} row-major in
+// shared memory (B rows of linv_ld(B) double-floats, zeros above the
+// diagonal, as stored by the initial solve).  Pair q comes interleaved,
+// UP[q][j] = (a_j.hi, b_j.hi, a_j.lo, b_j.lo); YP[q] is scratch of the same
+// form; the results go to Z[2q] (a) and Z[2q + 1] (b).  Y = X U row by row,
+// then Z = X^T Y column by column, with packed compensated sums.  A row of
+// i + 1 terms (a column of B - i) is split over 4 lanes, each taking every
+// fourth term, or over 2 lanes for the first r2 rows (the shortest), so that
+// one pass of the block covers all B rows: 4 (B - r2) + 2 r2 <= kThreads.
+// The 4-lane rows fill whole warps first, so that no row's lanes straddle a
+// warp; the lanes' partial sums are merged by shuffles, always in the same
+// order.
 template <int NP>
 __device__ void c0inv_apply(const df* X, int B, const float4* const* UP, float4* const* YP,
                             df* const* Z) {

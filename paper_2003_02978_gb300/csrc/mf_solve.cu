@@ -323,10 +323,13 @@ __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
   }
   __syncthreads();
   xtx_apply_df(A, B, invd, vt, vy, vz);  // z = (C^0)^{-1} t
-  const df q = block_dot_df(vt, vz, B, red);
-  const df muv = block_dot_df(vmf, vz, B, red);
-  const df coff = block_dot_df(vu3, vz, B, red);
-  const df n2 = block_dot_df(vmf, vmf, B, red);
+  __shared__ df s_d4[4];
+  {
+    const df* da[4] = {vt, vmf, vu3, vmf};
+    const df* db[4] = {vz, vz, vz, vmf};
+    multi_dot_df(da, db, 4, B, s_d4);
+  }
+  const df q = s_d4[0], muv = s_d4[1], coff = s_d4[2], n2 = s_d4[3];
   // store L^{-1} (row-major, lower with diagonal, rows padded to
   // linv_ld(B) entries), mean, target, solution
   const int xld = linv_ld(B);
