@@ -182,7 +182,7 @@ __device__ void reduce_k1(const Params& p, int part, const DfMat& A) {
 __device__ void assemble(const Params& p, const DfMat& A, const float* Q, const df* ub,
                          const df* u1, df invN, double* S_out, df* scratch) {
   const int B = p.B, K = p.K, W = K + 2;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   auto T = [&](int c, int i) -> df {
     if (c < K) return df{Q[c * B + i], 0.f};
     return c == K ? ub[i] : u1[i];
@@ -199,21 +199,24 @@ __device__ void assemble(const Params& p, const DfMat& A, const float* Q, const 
     P[idx] = v;
   }
   __syncthreads();
-  for (int j = warp; j < B; j += kWarps) {
-    for (int i = j + lane; i < B; i += 32) {
-      df v = A.get(j, i);  // G_ji = G_ij
-      for (int c = 0; c < W; ++c) {
-        if (c == K && !ub) continue;
-        v = df_fma(T(c, j), P[c * B + i], v);
-        v = df_fma(T(c, i), A.get(B + c, j), v);
-      }
-      v = df_mul(v, invN);
-      A.set(j, i, v);
-      if (S_out) {
-        const double d = df_to_double(v);
-        S_out[(size_t)i * B + j] = d;
-        S_out[(size_t)j * B + i] = d;
-      }
+  // the upper triangle's entries (row j, column i >= j, row-major) spread
+  // evenly over the block
+  const int ntri = B * (B + 1) / 2;
+  for (int t = tid; t < ntri; t += kThreads) {
+    int j, i;
+    tri_decode(t, B, j, i);
+    df v = A.get(j, i);  // G_ji = G_ij
+    for (int c = 0; c < W; ++c) {
+      if (c == K && !ub) continue;
+      v = df_fma(T(c, j), P[c * B + i], v);
+      v = df_fma(T(c, i), A.get(B + c, j), v);
+    }
+    v = df_mul(v, invN);
+    A.set(j, i, v);
+    if (S_out) {
+      const double d = df_to_double(v);
+      S_out[(size_t)i * B + j] = d;
+      S_out[(size_t)j * B + i] = d;
     }
   }
   __syncthreads();
@@ -283,7 +286,6 @@ __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
   pdl_trigger();
   const LaunchSpan span(p);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ df red[kWarps];
   const int part = blockIdx.x;
   const int tid = threadIdx.x;
   const int B = p.B, BA = p.BA, K = p.K;
