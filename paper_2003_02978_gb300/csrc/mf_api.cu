@@ -476,7 +476,7 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
       {(void**)&p.tprev, P * B * sizeof(float2)},
       {(void**)&p.muk, P * B * sizeof(float2)},
       {(void**)&p.S, P * B * B * sizeof(double)},
-      {(void**)&p.Linv, P * B * (B + 1) * sizeof(float2)},
+      {(void**)&p.Linv, P * ((size_t)B * (B + 1) / 2) * sizeof(float2)},  // packed rows
       {(void**)&p.pscal, P * 4 * sizeof(float)},
       {(void**)&p.dscal, P * 4 * sizeof(double)},
       {(void**)&p.k1part, (size_t)k1u * K1E * sizeof(float2)},

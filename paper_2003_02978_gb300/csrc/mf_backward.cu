@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 4) bwd_solve_kernel(Params p, BwdPar
     if (tid == 0) ps[PSC_ZT] = ps[PSC_ZMU0] = ps[PSC_ZOFF] = ps[PSC_PSUM] = ps[PSC_QBAR] = 0.0;
     return;
   }
-  df* X = reinterpret_cast<df*>(smem_raw);  // L^{-1} (ld linv_ld(B)), later the direct path's matrix
+  df* X = reinterpret_cast<df*>(smem_raw);  // L^{-1} (packed rows), later the direct path's matrix
   float4* UP0 = reinterpret_cast<float4*>(X + (size_t)B * linv_ld(B));  // (vbar, g) interleaved
   float4* UP1 = UP0 + B;                                               // (t^k, d) interleaved
   float4* YP0 = UP1 + B;
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 4) bwd_solve_kernel(Params p, BwdPar
   // L^{-1} of the partition into shared memory by one bulk copy, in flight
   // during the reductions below
   if (tid == 0) {
-    const size_t n = (size_t)B * linv_ld(B);
+    const size_t n = linv_packed(B);
     const uint32_t bytes = (uint32_t)(n * sizeof(float2));
     mbar_init(&s_xbar, 1);
     mbar_fence_init();

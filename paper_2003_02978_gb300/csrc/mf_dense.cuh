@@ -370,13 +370,18 @@ __device__ inline void xtx_apply_df(const DfMat& A, int n, const df* invd, const
   __syncthreads();
 }
 
-// row stride (double-floats) of the stored inverse factor: B + 1 keeps the
-// row walk and the column walk of c0inv_apply free of bank conflicts
+// row stride (double-floats) of the B x B scratch matrix the solve kernels
+// keep in the region that first holds L^{-1}
 __host__ __device__ inline int linv_ld(int B) { return B + 1; }
+// The stored inverse factor X = L^{-1} is packed: row i (its i + 1 entries
+// j <= i, the diagonal last) starts at i (i + 1) / 2, B (B + 1) / 2
+// double-floats in all (a multiple of 16 bytes for B a multiple of 4), half
+// the bytes the iteration solves copy per partition of a padded square.
+__host__ __device__ inline int linv_row(int i) { return i * (i + 1) / 2; }
+__host__ __device__ inline size_t linv_packed(int B) { return (size_t)B * (B + 1) / 2; }
 
-// Z = C^{-1} [a, b] for NP pairs of vectors, with X = L^{-1} row-major in
-// shared memory (B rows of linv_ld(B) double-floats, zeros above the
-// diagonal, as stored by the initial solve).  Pair q comes interleaved,
+// Z = C^{-1} [a, b] for NP pairs of vectors, with X = L^{-1} packed by rows
+// in shared memory (linv_row, as stored by the initial solve).  Pair q comes interleaved,
 // UP[q][j] = (a_j.hi, b_j.hi, a_j.lo, b_j.lo); YP[q] is scratch of the same
 // form; the results go to Z[2q] (a) and Z[2q + 1] (b).  Y = X U row by row,
 // then Z = X^T Y column by column, with packed compensated sums.  A row of
@@ -390,14 +395,14 @@ template <int NP>
 __device__ void c0inv_apply(const df* X, int B, const float4* const* UP, float4* const* YP,
                             df* const* Z) {
   static_assert(kThreads >= 2 * kMaxB, "two lanes per row at the widest window");
-  const int tid = threadIdx.x, ld = linv_ld(B);
+  const int tid = threadIdx.x;
   int r, sub, nl;
   apply_lanes(B, tid, r, sub, nl);
   for (int q = 0; q < NP; ++q) {
     Dot2x2 d;
     if (r >= 0) {
       const int i = r;
-      const df* row = X + (size_t)i * ld;
+      const df* row = X + linv_row(i);
       const float4* u = UP[q];
 #pragma unroll 4
       for (int j = sub; j <= i; j += nl) {
@@ -422,7 +427,7 @@ __device__ void c0inv_apply(const df* X, int B, const float4* const* UP, float4*
 #pragma unroll 4
       for (int i = j + sub; i < B; i += nl) {
         const float4 yy = y[i];
-        d.add(X[(size_t)i * ld + j], make_float2(yy.x, yy.y), make_float2(yy.z, yy.w));
+        d.add(X[linv_row(i) + j], make_float2(yy.x, yy.y), make_float2(yy.z, yy.w));
       }
     }
     merge_apply_lanes(d, nl);

@@ -332,14 +332,15 @@ __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
     multi_dot_df(da, db, 4, B, s_d4);
   }
   const df q = s_d4[0], muv = s_d4[1], coff = s_d4[2], n2 = s_d4[3];
-  // store L^{-1} (row-major, lower with diagonal, rows padded to
-  // linv_ld(B) entries), mean, target, solution
-  const int xld = linv_ld(B);
-  float2* X = p.Linv + (size_t)part * B * xld;
-  for (int idx = tid; idx < B * xld; idx += kThreads) {
-    const int i = idx / xld, j = idx - i * xld;
-    const df v = (j < i) ? A.get(i, j) : (j == i ? invd[i] : df{0.f, 0.f});
-    stf(X, idx, v);
+  // store L^{-1} (packed rows: linv_row), mean, target, solution
+  const size_t xn = linv_packed(B);
+  float2* X = p.Linv + (size_t)part * xn;
+  for (int idx = tid; idx < (int)xn; idx += kThreads) {
+    int i = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);  // row: linv_row(i) <= idx
+    if (linv_row(i) > idx) --i;
+    else if (linv_row(i + 1) <= idx) ++i;
+    const int j = idx - linv_row(i);
+    stf(X, idx, j < i ? A.get(i, j) : invd[i]);
   }
   for (int b = tid; b < B; b += kThreads) {
     stf(p.mu0, pb + b, vmu[b]);
@@ -391,8 +392,7 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
   const int B = p.B;
   const size_t pb = (size_t)part * B;
   if (pass > p.lines[part_line(p, part)].n_iter) return;  // the line's iterations are done
-  // L^{-1} (B rows of linv_ld(B) double-floats), later the direct path's
-  // B x B matrix
+  // L^{-1} (packed rows, linv_row), later the direct path's B x B matrix
   df* X = reinterpret_cast<df*>(smem_raw);
   float4* UP = reinterpret_cast<float4*>(X + (size_t)B * linv_ld(B));  // (g, t^{k+1}) interleaved
   float4* YP = UP + B;
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
   // during the moment reduction
   const bool solve = mode != SOLVE_MEAN_ONLY;
   if (solve && tid == 0) {
-    const size_t n = (size_t)B * linv_ld(B);
+    const size_t n = linv_packed(B);
     const uint32_t bytes = (uint32_t)(n * sizeof(float2));
     mbar_init(&s_xbar, 1);
     mbar_fence_init();
@@ -513,9 +513,17 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
   __shared__ df s_A3[9];
   __shared__ df s_rhs[3];
   {
-    const df* ua[9] = {U0, U0, U0, U1, U1, U1, U2, U2, U2};
-    const df* zb[9] = {Z0, Z1, Z2, Z0, Z1, Z2, Z0, Z1, Z2};
-    multi_dot_df(ua, zb, 9, B, s_W);
+    // W = U^T C0^{-1} U is symmetric: its six distinct entries, one warp
+    // each (one round for eight warps), mirrored below the diagonal
+    const df* ua[6] = {U0, U0, U0, U1, U1, U2};
+    const df* zb[6] = {Z0, Z1, Z2, Z1, Z2, Z2};
+    __shared__ df s_w6[6];
+    multi_dot_df(ua, zb, 6, B, s_w6);
+    if (tid < 9) {
+      const int i = tid / 3, j = tid % 3, a = min(i, j), c = max(i, j);
+      s_W[tid] = s_w6[a == 0 ? c : (a == 1 ? 2 + c : 5)];
+    }
+    __syncthreads();
   }
   // C = C0 + U M U^T;  v = z_t - Z (I + M W)^{-1} M W[:, 1].  Warp 0: lane
   // (i, j) < 9 forms (I + M W)_ij, then the 3x3 system by Cramer's rule.
