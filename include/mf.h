@@ -133,6 +133,21 @@ mf_status mf_retrieve_host(mf_plan_t plan, const float* cube, const float* k, do
                            double eps, int32_t n_iter, const uint8_t* mask,
                            float* alpha_out, void* stream);
 
+/* mf_retrieve_host for a stream of cubes: the same arguments (HOST
+ * pointers; cube, mask and alpha_out in pinned memory for the copies to be
+ * asynchronous), but the call returns without synchronising, so that the
+ * copy of the next call's cube overlaps this call's retrieval.  Two sets of
+ * plan-owned device staging (allocated on the first call, 2 x (cube + mask
+ * + alpha) bytes) alternate between calls, with a plan-owned copy stream:
+ * call n copies its inputs in on that stream once call n - 2's retrieval
+ * and output copy are done, the retrieval and the copy of alpha out run on
+ * `stream` after the inputs have landed.  alpha_out holds the result once
+ * `stream` has been synchronised after the call; the host buffers must stay
+ * alive and unchanged until then.  Errors as mf_retrieve_host. */
+mf_status mf_retrieve_host_async(mf_plan_t plan, const float* cube, const float* k, double lambda,
+                                 double eps, int32_t n_iter, const uint8_t* mask,
+                                 float* alpha_out, void* stream);
+
 /* mf_retrieve (no alpha_init, no albedo output) that also writes the
  * objective of every iterate, the energy whose decrease Fig. 5 tracks (Sec.
  * III-B): for iterate k = 0..n_iter of partition j,

@@ -150,6 +150,27 @@ class Plan:
               "mf_retrieve_host")
         return out
 
+    def retrieve_host_async(self, cube, k, lam, eps, n_iter, mask=None, out=None, stream=None):
+        """Host-buffer retrieval for a stream of cubes (mf_retrieve_host_async):
+        cube, mask and out pinned CPU tensors; returns at once, the copy of
+        the next call's cube overlapping this call's retrieval.  ``out`` holds
+        alpha once ``stream`` (default: the current stream) is synchronised;
+        the tensors must stay alive and unchanged until then."""
+        s = self.shape
+        assert cube.dtype == torch.float32 and cube.is_contiguous() and cube.is_pinned()
+        k = torch.as_tensor(np.asarray(k, dtype=np.float32)).contiguous()
+        if mask is not None:
+            assert mask.dtype == torch.uint8 and mask.is_contiguous() and mask.is_pinned()
+        if out is None:
+            out = torch.empty((s.rows, s.cols), dtype=torch.float32).pin_memory()
+        assert out.is_pinned()
+        self._async_k = k  # kept alive with the call (its copy is staged)
+        check(lib().mf_retrieve_host_async(self._h, _ptr(cube), _ptr(k), float(lam), float(eps),
+                                           int(n_iter), _ptr(mask), _ptr(out),
+                                           _stream_handle(stream)),
+              "mf_retrieve_host_async")
+        return out
+
     def ckpt_bytes(self, n_iter, cube_grad=False) -> int:
         return int(lib().mf_ckpt_bytes(self._h, int(n_iter), int(bool(cube_grad))))
 

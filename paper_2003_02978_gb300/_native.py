@@ -50,6 +50,9 @@ def lib() -> ctypes.CDLL:
     L.mf_retrieve_host.argtypes = [c_void_p, fp, fp, c_double, c_double, c_int32, fp, fp,
                                    c_void_p]
     L.mf_retrieve_host.restype = c_int
+    L.mf_retrieve_host_async.argtypes = [c_void_p, fp, fp, c_double, c_double, c_int32, fp, fp,
+                                         c_void_p]
+    L.mf_retrieve_host_async.restype = c_int
     L.mf_background.argtypes = [c_void_p, fp, fp, c_void_p]
     L.mf_background.restype = c_int
     L.mf_plan_status.argtypes = [c_void_p, POINTER(c_int32)]

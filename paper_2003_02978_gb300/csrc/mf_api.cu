@@ -94,8 +94,12 @@ struct mf_plan_s {
   // serialisation (MF_PDL=0 at plan creation: off)
   bool pdl = true;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  GraphKey gkey{};
+  // two graphs (keyed by pointers, pass count, eps, timeline): the
+  // double-buffered host entry point alternates between two sets of buffers
+  static constexpr int kGraphs = 2;
+  cudaGraphExec_t gexec[kGraphs] = {};
+  GraphKey gkey[kGraphs]{};
+  int gnext = 0;  // the slot a new key replaces
   // tensor maps of the last cube pointer (re-encoded when it changes)
   const float* map_cube = nullptr;
   CUtensorMap map_stats{}, map_pixel{};
@@ -107,6 +111,16 @@ struct mf_plan_s {
   uint8_t* h_mask = nullptr;
   float* h_k = nullptr;
   float* h_alpha = nullptr;
+  // double-buffered staging of mf_retrieve_host_async: slot b's device
+  // buffers, a copy stream, and per slot the events "copied in" and
+  // "consumed" (its retrieval and the copy of alpha out have finished)
+  float* a_cube[2] = {nullptr, nullptr};
+  uint8_t* a_mask[2] = {nullptr, nullptr};
+  float* a_k[2] = {nullptr, nullptr};
+  float* a_alpha[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+  int aslot = 0;
   // kernel timing (mf_profile)
   bool profile = false;
   struct Mark {
@@ -598,10 +612,15 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
   } else {
     const mf_plan_s::GraphKey key{{cube, k, mask, alpha_init, alpha_out, albedo_out},
                                   n_iter_max, (float)eps, pl->timeline};
-    if (!pl->gexec || !(key == pl->gkey)) {
-      if (pl->gexec) {
-        MF_CUDA(cudaGraphExecDestroy(pl->gexec));
-        pl->gexec = nullptr;
+    int gi = -1;
+    for (int i = 0; i < mf_plan_s::kGraphs; ++i)
+      if (pl->gexec[i] && key == pl->gkey[i]) gi = i;
+    if (gi < 0) {
+      gi = pl->gnext;
+      pl->gnext = (pl->gnext + 1) % mf_plan_s::kGraphs;
+      if (pl->gexec[gi]) {
+        MF_CUDA(cudaGraphExecDestroy(pl->gexec[gi]));
+        pl->gexec[gi] = nullptr;
       }
       if (!pl->cap_stream) MF_CUDA(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
       cudaGraph_t g = nullptr;
@@ -609,15 +628,15 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
       enqueue(pl->cap_stream);
       const cudaError_t e1 = cudaStreamEndCapture(pl->cap_stream, &g);
       if (e1 != cudaSuccess) return fail(MF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e1));
-      const cudaError_t e2 = cudaGraphInstantiate(&pl->gexec, g, 0);
+      const cudaError_t e2 = cudaGraphInstantiate(&pl->gexec[gi], g, 0);
       cudaGraphDestroy(g);
       if (e2 != cudaSuccess) {
-        pl->gexec = nullptr;
+        pl->gexec[gi] = nullptr;
         return fail(MF_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e2));
       }
-      pl->gkey = key;
+      pl->gkey[gi] = key;
     }
-    MF_CUDA(cudaGraphLaunch(pl->gexec, s));
+    MF_CUDA(cudaGraphLaunch(pl->gexec[gi], s));
   }
   pl->last_stream = s;
   return MF_OK;
@@ -675,7 +694,17 @@ void mf_destroy(mf_plan_t pl) {
   cudaFree(pl->h_alpha);
   if (pl->lines_pinned) cudaFreeHost(pl->lines_pinned);
   if (pl->lines_copied) cudaEventDestroy(pl->lines_copied);
-  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  for (auto& g : pl->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(pl->a_cube[b]);
+    cudaFree(pl->a_mask[b]);
+    cudaFree(pl->a_k[b]);
+    cudaFree(pl->a_alpha[b]);
+    if (pl->copied[b]) cudaEventDestroy(pl->copied[b]);
+    if (pl->consumed[b]) cudaEventDestroy(pl->consumed[b]);
+  }
+  if (pl->copy_stream) cudaStreamDestroy(pl->copy_stream);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   cudaFree(pl->tl_dev);
   delete pl;
@@ -917,6 +946,48 @@ mf_status mf_retrieve_host(mf_plan_t pl, const float* cube, const float* k, doub
   MF_CUDA(cudaMemcpyAsync(alpha_out, pl->h_alpha, npix * sizeof(float), cudaMemcpyDeviceToHost,
                           s));
   MF_CUDA(cudaStreamSynchronize(s));
+  return MF_OK;
+}
+
+mf_status mf_retrieve_host_async(mf_plan_t pl, const float* cube, const float* k, double lambda,
+                                 double eps, int32_t n_iter, const uint8_t* mask,
+                                 float* alpha_out, void* stream) {
+  g_last_error.clear();
+  if (!pl || !cube || !k || !alpha_out) return fail(MF_ERR_INVALID_ARG, "null argument");
+  const mf::Params& g = pl->prm;
+  const size_t npix = (size_t)g.rows * g.cols;
+  const size_t cube_bytes = npix * g.bands_total * sizeof(float);
+  if (!pl->copy_stream) {
+    for (int b = 0; b < 2; ++b) {
+      MF_CUDA(cudaMalloc(&pl->a_cube[b], cube_bytes));
+      MF_CUDA(cudaMalloc(&pl->a_mask[b], npix));
+      MF_CUDA(cudaMalloc(&pl->a_k[b], (size_t)g.B * sizeof(float)));
+      MF_CUDA(cudaMalloc(&pl->a_alpha[b], npix * sizeof(float)));
+      MF_CUDA(cudaEventCreateWithFlags(&pl->copied[b], cudaEventDisableTiming));
+      MF_CUDA(cudaEventCreateWithFlags(&pl->consumed[b], cudaEventDisableTiming));
+    }
+    MF_CUDA(cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking));
+  }
+  const int b = pl->aslot;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // slot b's buffers are free once the retrieval that last used them and
+  // its copy of alpha out are done (an event never recorded: no wait)
+  MF_CUDA(cudaStreamWaitEvent(pl->copy_stream, pl->consumed[b], 0));
+  MF_CUDA(cudaMemcpyAsync(pl->a_cube[b], cube, cube_bytes, cudaMemcpyHostToDevice, pl->copy_stream));
+  MF_CUDA(cudaMemcpyAsync(pl->a_k[b], k, (size_t)g.B * sizeof(float), cudaMemcpyHostToDevice,
+                          pl->copy_stream));
+  if (mask)
+    MF_CUDA(cudaMemcpyAsync(pl->a_mask[b], mask, npix, cudaMemcpyHostToDevice, pl->copy_stream));
+  MF_CUDA(cudaEventRecord(pl->copied[b], pl->copy_stream));
+  MF_CUDA(cudaStreamWaitEvent(s, pl->copied[b], 0));
+  mf_status st = mf_retrieve(pl, pl->a_cube[b], pl->a_k[b], lambda, eps, n_iter,
+                             mask ? pl->a_mask[b] : nullptr, nullptr, pl->a_alpha[b], nullptr,
+                             stream);
+  if (st != MF_OK) return st;
+  MF_CUDA(cudaMemcpyAsync(alpha_out, pl->a_alpha[b], npix * sizeof(float), cudaMemcpyDeviceToHost,
+                          s));
+  MF_CUDA(cudaEventRecord(pl->consumed[b], s));
+  pl->aslot = b ^ 1;
   return MF_OK;
 }
 
