@@ -613,6 +613,14 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
         en[pass - 1] += df_to_double(mom[B + 3]);  // the previous pass's pixel terms
       }
     }
+  } else {
+    // warps 1-7, idle while warp 0 solves: the outputs that do not depend
+    // on its solution (the same on the direct path)
+    for (int i = tid - 32; i < B; i += kThreads - 32) {
+      stf(p.zt, pb + i, Z1[i]);
+      stf(p.tprev, pb + i, U1[i]);
+      stf(p.muk, pb + i, vmk[i]);
+    }
   }
   __syncthreads();
   if (s_bad == 1) {
@@ -657,12 +665,7 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
     multi_dot_df(da, db, 3, B, s_d3);
   }
   const df q = s_d3[0], muv = s_d3[1], coff = s_d3[2];
-  for (int i = tid; i < B; i += kThreads) {
-    p.vf[pb + i] = df_to_float(vv[i]);
-    stf(p.zt, pb + i, Z1[i]);
-    stf(p.tprev, pb + i, U1[i]);
-    stf(p.muk, pb + i, vmk[i]);
-  }
+  for (int i = tid; i < B; i += kThreads) p.vf[pb + i] = df_to_float(vv[i]);
   if (p.ck_vec && pass < p.ck_stages) {  // checkpoint of stage `pass`
     float2* cv = p.ck_vec + ((size_t)part * p.ck_stages + pass) * 4 * B;
     for (int i = tid; i < B; i += kThreads) {
