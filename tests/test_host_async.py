@@ -44,3 +44,22 @@ def test_async_host_calls_match_sync(mfg, precision):
     for i, j in enumerate(order):
         assert torch.equal(outs[i], ref[j]), (i, j)
     plan.close()
+
+
+def test_async_host_without_mask_and_changing_iterations(mfg):
+    scenes = [workload_scene("plain-512x16x72", seed=s, device="cpu") for s in (4, 5)]
+    rows, cols, bands = scenes[0][0].cube.shape
+    plan = mfg.Plan(rows, cols, bands)
+    calls = [(0, 2), (1, 3), (0, 3), (1, 0)]  # (scene, n_iter)
+    ref = [plan.retrieve_host(scenes[j][0].cube.contiguous(), scenes[j][0].k,
+                              scenes[j][1]["lam"], scenes[j][1]["eps"], n).clone()
+           for j, n in calls]
+    pinned = [sc.cube.contiguous().pin_memory() for sc, _ in scenes]
+    outs = [torch.empty((rows, cols), dtype=torch.float32).pin_memory() for _ in calls]
+    for i, (j, n) in enumerate(calls):
+        sc, prm = scenes[j]
+        plan.retrieve_host_async(pinned[j], sc.k, prm["lam"], prm["eps"], n, out=outs[i])
+    torch.cuda.current_stream().synchronize()
+    for i in range(len(calls)):
+        assert torch.equal(outs[i], ref[i]), i
+    plan.close()
