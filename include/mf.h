@@ -88,7 +88,11 @@ typedef struct {
  * caller and released with mf_destroy.
  * Environment read here (all optional): MF_GRAPH=0 launches the kernels
  * directly instead of replaying a CUDA graph; MF_RB_ROWS / MF_SC_ROWS set the
- * rows per pixel-kernel CTA / per statistics item (as mf_tuning);
+ * rows per pixel-kernel CTA / per statistics item (as mf_tuning); MF_PDL=0
+ * launches every kernel in plain stream order (default: programmatic
+ * dependent launch for the statistics and solve kernels); MF_PF_STAGES (default
+ * 4, 0 = off) sets how many stages of every pixel-kernel CTA the solve
+ * kernels prefetch into L2 for the pass that follows them;
  * MF_FORCE_DIRECT=1 (a test hook) sends every fused iteration's solve through
  * the direct factorisation of C^k that otherwise serves only ill-conditioned
  * Woodbury systems.  MF_FAULT (a fault-injection hook for tests; nothing in

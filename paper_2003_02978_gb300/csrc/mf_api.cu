@@ -375,6 +375,7 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   pl->nj = nj_bucket(p.B4);
   pl->use_graph = env_int("MF_GRAPH", 1) != 0;
   pl->pdl = env_int("MF_PDL", 1) != 0;
+  p.pf_stages = env_int("MF_PF_STAGES", 4);
   if (tune && tune->use_graph < 0) pl->use_graph = false;
 
   cudaError_t e = cudaGetDevice(&pl->device);

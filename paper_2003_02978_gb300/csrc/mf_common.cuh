@@ -134,6 +134,9 @@ struct Params {
   int tl_slot;
   // launch with programmatic stream serialisation (see pdl_wait)
   int pdl;
+  // the solve kernels prefetch into L2 the first pf_stages stages of every
+  // pixel CTA of the pass that follows them (0: off; single-line plans)
+  int pf_stages;
 };
 
 // Programmatic dependent launch.  A kernel launched with the programmatic

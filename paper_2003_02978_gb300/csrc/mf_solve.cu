@@ -80,6 +80,43 @@ __device__ df block_dot_df(const df* a, const df* b, int n, df* red) {
   return block_sum_df(d.result(), red);
 }
 
+// bulk prefetch of `bytes` (a multiple of 16) at `src` (16-byte aligned)
+// into L2; no completion to wait for
+__device__ __forceinline__ void prefetch_l2_bulk(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// While a solve kernel runs, the HBM would otherwise idle: at its start
+// (before its dependency wait: the cube is read-only), prefetch into L2 the
+// first p.pf_stages stages (8 rows of a 16-column tile each) of every CTA of
+// the pixel pass `pass` that follows, in that pass's row order, so that the
+// pass finds them there.  Items (pixel CTA, stage) are spread over the
+// solve's CTAs; threads 0-7 take a stage's rows, one bulk prefetch of the
+// tile's contiguous row segment each.  Single-line plans only.  Measured on
+// the flightline: 4 stages (45 MB per pass) take 12 us off the pixel passes
+// of a retrieval and cost the solves 2 us; deeper prefetch, or prefetch
+// issued after the wait, slows the solves more than it helps the passes.
+__device__ void prefetch_pixel_pass(const Params& p, int pass) {
+  if (p.pf_stages <= 0 || p.n_lines != 1 || threadIdx.x >= kStageRows) return;
+  const LineInfo& line = p.line0;
+  const bool backwards = (pass & 1) != 0;
+  const int items = p.n_blocks * p.pf_stages;
+  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+    const int b = w % p.n_blocks, i = w / p.n_blocks;
+    const int local = b - line.blk0;
+    const int ct = local % p.n_ct, rb = local / p.n_ct;
+    const int c0t = ct * kTileCols, nc = min(kTileCols, p.cols - c0t);
+    const int r_beg = line.row0 + rb * line.rb_rows;
+    const int r_end = min(line.row0 + line.rows, r_beg + line.rb_rows);
+    const int nst = (r_end - r_beg + kStageRows - 1) / kStageRows;
+    if (i >= nst) continue;
+    const int r = r_beg + (backwards ? nst - 1 - i : i) * kStageRows + threadIdx.x;
+    if (r < r_end)
+      prefetch_l2_bulk(p.cube + ((size_t)r * p.cols + c0t) * p.bands_total,
+                       (uint32_t)(nc * p.bands_total * sizeof(float)));
+  }
+}
+
 // reduce the per-CTA augmented moments of `part` into the full symmetric
 // BA x BA matrix A; each thread keeps 2 x 8 loads in flight
 __device__ void reduce_k1(const Params& p, int part, const DfMat& A) {
@@ -282,6 +319,7 @@ size_t solve_literal_smem_bytes(int B, int BA) {
 }
 
 __global__ void __launch_bounds__(kThreads, 4) solve_init_kernel(Params p) {
+  prefetch_pixel_pass(p, 0);  // the cube only: no need to wait
   pdl_wait();
   pdl_trigger();
   const LaunchSpan span(p);
@@ -436,6 +474,7 @@ __global__ void __launch_bounds__(kThreads, 4) solve_iter_kernel(Params p, int m
   }
   // all of the above comes from kernels two or more launches back; the
   // moments, the status and every write below wait for the pixel pass
+  if (mode != SOLVE_MEAN_ONLY) prefetch_pixel_pass(p, pass);
   pdl_wait();
   pdl_trigger();
   const LaunchSpan span(p);
