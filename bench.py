@@ -92,6 +92,7 @@ def source_hash(files):
 # capture summarised in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum).
 # Valid only while the kernel source is unchanged (hash of the files below).
 PIXEL_KERNEL_SOURCES = ["paper_2003_02978_gb300/csrc/mf_pixel.cu",
+                        "paper_2003_02978_gb300/csrc/mf_pixel_body.cuh",
                         "paper_2003_02978_gb300/csrc/mf_pixel_io.cuh",
                         "paper_2003_02978_gb300/csrc/mf_tma.cuh",
                         "paper_2003_02978_gb300/csrc/mf_common.cuh"]
@@ -464,7 +465,7 @@ def batched_form(dev, precision, n_lines=BATCH_LINES):
     tuning = tune.autotune(cube, k, lams, 1e-9, nits, mask=mask, line_rows=rows,
                            precision=precision, reps=1, use_cache=False,
                            candidates=[(0, 0), (256, 0), (512, 0), (0, 512), (256, 512),
-                                       (512, 512)])
+                                       (512, 512), (0, 0, 1)])
     tune_s = time.perf_counter() - t0
     plan = mfg.BatchPlan(rows, cols, bands, precision=precision, tuning=tuning)
     out = torch.empty((R, cols), dtype=torch.float32, device=dev)
@@ -476,6 +477,21 @@ def batched_form(dev, precision, n_lines=BATCH_LINES):
     status_ok = bool(np.all(plan.status() == 0))
     slices = plan.line_slices()
     plan.close()
+    # the other schedule with the same shapes: one launch per pass (a CUDA
+    # graph of ~2 n_iter launches) or the persistent work queue (one launch
+    # after the statistics); the same arithmetic, so bit-identical alpha
+    other = dict(tuning, persistent=0 if tuning.get("persistent") else 1)
+    plan_o = mfg.BatchPlan(rows, cols, bands, precision=precision, tuning=other)
+    out_o = torch.empty_like(out)
+
+    def run_o(pl):
+        pl.retrieve(cube, k, lams, 1e-9, nits, mask=mask, out=out_o)
+
+    ms_o = time_retrievals(plan_o, run_o, 3, 2, dev)
+    same_bits = bool(torch.equal(out.view(torch.int32), out_o.view(torch.int32)))
+    plan_o.close()
+    del out_o
+    ms_seq, ms_queue = (ms_o, ms_b) if tuning.get("persistent") else (ms_b, ms_o)
     # plain FP32 form: literal schedule, one plan per line
     outp = torch.empty_like(out)
     ms_p = 0.0
@@ -507,6 +523,10 @@ def batched_form(dev, precision, n_lines=BATCH_LINES):
            "precision": "bf16split" if precision else "fp32",
            "tuning": tuning, "autotune_s": tune_s,
            "value": npix / (ms_b * 1e-3) / 1e6, "ms_per_batch": ms_b,
+           "schedule": "persistent work queue" if tuning.get("persistent") else "launch per pass",
+           "launch_per_pass_value": npix / (ms_seq * 1e-3) / 1e6,
+           "persistent_value": npix / (ms_queue * 1e-3) / 1e6,
+           "schedules_bit_identical": same_bits,
            "plain_fp32_value": npix / (ms_p * 1e-3) / 1e6, "plain_fp32_ms": ms_p,
            "status_ok": status_ok}
     return res, {"k": k_np, "samples": samples}

@@ -67,6 +67,14 @@ enum { MF_FP32 = 0, MF_BF16SPLIT = 1 };
                                     iteration, as Fig. 1 prints it; off: exact rank-3 update of
                                     C^0 (same result up to rounding) */
 #define MF_PENALTY_NO_ALBEDO 8u  /* penalty lambda*w_i/r_i instead of lambda*w_i */
+#define MF_PERSISTENT       16u  /* after the statistics pass, one persistent launch runs the
+                                    initial solves, every pixel pass and every iteration solve
+                                    of every line as work items of a dependency-ordered queue
+                                    (same results, bit for bit, as the launch-per-pass
+                                    sequence); not with MF_LITERAL.  Each dependency wait is
+                                    bounded (MF_QUEUE_WAIT_MS, default 2000): one that runs out
+                                    stops the queue and every partition's status reads
+                                    MF_ERR_TIMEOUT */
 
 typedef struct {
   int64_t rows;         /* along-track lines */
@@ -77,7 +85,8 @@ typedef struct {
   int32_t col_group;    /* adjacent detectors per partition (>= 1) */
   int32_t layout;       /* MF_BIP */
   int32_t precision;    /* MF_FP32 | MF_BF16SPLIT */
-  uint32_t flags;       /* MF_ALBEDO | MF_SPARSE | MF_LITERAL | MF_PENALTY_NO_ALBEDO */
+  uint32_t flags;       /* MF_ALBEDO | MF_SPARSE | MF_LITERAL | MF_PENALTY_NO_ALBEDO |
+                           MF_PERSISTENT */
 } mf_desc;
 
 /* Validate the descriptor and allocate every device buffer a retrieval of

@@ -19,6 +19,7 @@ ALBEDO = 1
 SPARSE = 2
 LITERAL = 4
 PENALTY_NO_ALBEDO = 8
+PERSISTENT = 16  # one work-queue launch after the statistics pass (fused schedule)
 FP32 = 0
 BF16SPLIT = 1
 DEFAULT_FLAGS = ALBEDO | SPARSE
@@ -33,7 +34,7 @@ TABLE_I = {
     "albedo_rwl1mf": (True, ALBEDO | SPARSE),
 }
 
-__all__ = ["Plan", "BatchPlan", "Retrieve", "retrieve_differentiable", "retrieve", "MFError", "ALBEDO", "SPARSE", "LITERAL", "PENALTY_NO_ALBEDO",
+__all__ = ["Plan", "BatchPlan", "Retrieve", "retrieve_differentiable", "retrieve", "MFError", "ALBEDO", "SPARSE", "LITERAL", "PENALTY_NO_ALBEDO", "PERSISTENT",
            "FP32", "BF16SPLIT", "TABLE_I", "library_path"]
 
 
@@ -42,8 +43,17 @@ def library_path() -> str:
     return LIB_PATH
 
 
+_KINDS = ("stats", "pixel", "solve", "queue")  # launch kinds of the profile and timeline
+
+
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _flags(flags, tuning) -> int:
+    """Plan flags, with PERSISTENT when the tuning asks for the work-queue
+    schedule (``tuning["persistent"]``, as the autotuner may choose)."""
+    return int(flags) | (PERSISTENT if (tuning or {}).get("persistent") else 0)
 
 
 def _tuning(t) -> MfTuning:
@@ -76,6 +86,7 @@ class Plan:
     def __init__(self, rows, cols, bands_total, band_lo=0, band_hi=None, col_group=1,
                  flags=DEFAULT_FLAGS, precision=FP32, tuning=None):
         band_hi = bands_total if band_hi is None else band_hi
+        flags = _flags(flags, tuning)
         self.shape = Shape(int(rows), int(cols), int(bands_total), int(band_lo), int(band_hi),
                            int(col_group), int(flags), int(precision))
         d = MfDesc(rows=rows, cols=cols, bands_total=bands_total, band_lo=band_lo,
@@ -246,11 +257,12 @@ class Plan:
         check(lib().mf_profile(self._h, int(enable)), "mf_profile")
 
     def profile_read(self):
-        """{'stats'|'pixel'|'solve': (ms, launches)} since the last read."""
-        ms = (ctypes.c_double * 3)()
-        n = (ctypes.c_int64 * 3)()
-        check(lib().mf_profile_read(self._h, ms, n, 3), "mf_profile_read")
-        return {"stats": (ms[0], n[0]), "pixel": (ms[1], n[1]), "solve": (ms[2], n[2])}
+        """{'stats'|'pixel'|'solve'|'queue': (ms, launches)} since the last read
+        ('queue': the persistent work-queue launch of an MF_PERSISTENT plan)."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        check(lib().mf_profile_read(self._h, ms, n, 4), "mf_profile_read")
+        return {name: (ms[i], n[i]) for i, name in enumerate(_KINDS)}
 
     def timeline(self, enable: bool = True):
         """Device timeline of each retrieval as it runs (graph replay included)."""
@@ -258,7 +270,7 @@ class Plan:
 
     def timeline_read(self, cap: int = 4096):
         """[(kind, start_us, end_us)] of the last retrieval's launches, kind
-        'stats' | 'pixel' | 'solve', times after its earliest start (None for a
+        'stats' | 'pixel' | 'solve' | 'queue', times after its earliest start (None for a
         launch that ran no CTA); clears the timeline."""
         t0 = (ctypes.c_double * cap)()
         t1 = (ctypes.c_double * cap)()
@@ -266,8 +278,7 @@ class Plan:
         n = ctypes.c_int32(0)
         check(lib().mf_timeline_read(self._h, t0, t1, kd, int(cap), ctypes.byref(n)),
               "mf_timeline_read")
-        names = ("stats", "pixel", "solve")
-        return [(names[kd[i]], None if t0[i] < 0 else t0[i], None if t1[i] < 0 else t1[i])
+        return [(_KINDS[kd[i]], None if t0[i] < 0 else t0[i], None if t1[i] < 0 else t1[i])
                 for i in range(n.value)]
 
 
@@ -280,6 +291,7 @@ class BatchPlan(Plan):
                  flags=DEFAULT_FLAGS, precision=FP32, tuning=None):
         line_rows = [int(r) for r in line_rows]
         band_hi = bands_total if band_hi is None else band_hi
+        flags = _flags(flags, tuning)
         rows = sum(line_rows)
         self.shape = Shape(rows, int(cols), int(bands_total), int(band_lo), int(band_hi),
                            int(col_group), int(flags), int(precision))

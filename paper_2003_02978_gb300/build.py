@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmf.so")
 SOURCES = ["mf_api.cu", "mf_stats.cu", "mf_pixel.cu", "mf_solve.cu", "mf_noalloc.cu", "mf_stats_tc.cu",
-           "mf_backward.cu"]
+           "mf_backward.cu", "mf_queue.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-rdc=false"]

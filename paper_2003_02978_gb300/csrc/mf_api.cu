@@ -58,6 +58,10 @@ struct mf_plan_s {
   int nj = 0;             // template bucket
   size_t smem_stats = 0, smem_pixel = 0, smem_sinit = 0, smem_siter = 0, smem_slit = 0;
   int grid_stats = 0, grid_pixel = 0;
+  // persistent work queue (MF_PERSISTENT): one launch after the statistics
+  bool persistent = false;
+  size_t smem_queue = 0, q_bytes = 0;
+  int grid_queue = 0;
   // flightlines: host copy of the device table, pinned staging for the
   // per-call lambda / iteration counts, and the values last uploaded
   int n_lines = 1;
@@ -162,6 +166,10 @@ cudaError_t set_attrs(const mf_plan_s* pl) {
   if (e == cudaSuccess)
     e = mf::solve_set_attributes(mf::solve_init_smem_bytes(bmax, ba), mf::solve_iter_smem_bytes(bmax),
                                  mf::solve_literal_smem_bytes(bmax, ba));
+  if (e == cudaSuccess && pl->persistent)
+    e = mf::queue_set_attributes(
+        pl->nj, std::max({mf::pixel_smem_bytes(bmax_bucket, pl->nj), mf::solve_init_smem_bytes(bmax, ba),
+                          mf::solve_iter_smem_bytes(bmax)}));
   return e;
 }
 
@@ -221,7 +229,7 @@ void mark_end(mf_plan_s::Mark* m, cudaStream_t s) {
   if (m) cudaEventRecord(m->stop, s);
 }
 
-enum { KIND_STATS = 0, KIND_PIXEL = 1, KIND_SOLVE = 2, KIND_COUNT = 3 };
+enum { KIND_STATS = 0, KIND_PIXEL = 1, KIND_SOLVE = 2, KIND_QUEUE = 3, KIND_COUNT = 4 };
 
 constexpr size_t kMaxSpans = 4096;  // device timeline slots (launches per retrieval)
 
@@ -271,6 +279,12 @@ void solve_iter_dispatch(mf_plan_s* pl, const mf::Params& prm, int mode, int pas
                          cudaStream_t s) {
   mf_plan_s::Mark* m = mark_begin(pl, KIND_SOLVE, s);
   mf::solve_iter_launch(pl->smem_siter, s, span_params(pl, prm, KIND_SOLVE), mode, pass);
+  mark_end(m, s);
+}
+void queue_dispatch(mf_plan_s* pl, const mf::Params& prm, int n_iter_max, cudaStream_t s) {
+  mf_plan_s::Mark* m = mark_begin(pl, KIND_QUEUE, s);
+  mf::queue_launch(pl->nj, pl->grid_queue, pl->smem_queue, s, pl->map_pixel,
+                   span_params(pl, prm, KIND_QUEUE, true), n_iter_max);
   mark_end(m, s);
 }
 void solve_literal_dispatch(mf_plan_s* pl, const mf::Params& prm, int pass, cudaStream_t s) {
@@ -329,8 +343,10 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   if (d->layout != MF_BIP) return fail(MF_ERR_UNSUPPORTED, "only the BIP layout is supported");
   if (d->precision != MF_FP32 && d->precision != MF_BF16SPLIT)
     return fail(MF_ERR_INVALID_ARG, "unknown precision %d", d->precision);
-  if (d->flags & ~(MF_ALBEDO | MF_SPARSE | MF_LITERAL | MF_PENALTY_NO_ALBEDO))
+  if (d->flags & ~(MF_ALBEDO | MF_SPARSE | MF_LITERAL | MF_PENALTY_NO_ALBEDO | MF_PERSISTENT))
     return fail(MF_ERR_INVALID_ARG, "unknown flag bits 0x%x", d->flags);
+  if ((d->flags & MF_PERSISTENT) && (d->flags & MF_LITERAL))
+    return fail(MF_ERR_INVALID_ARG, "MF_PERSISTENT runs the fused schedule, not MF_LITERAL");
   const int B = d->band_hi - d->band_lo;
   if (B < 8 || B > mf::kMaxB || B % 4 || d->band_lo % 4 || d->bands_total % 4)
     return fail(MF_ERR_UNSUPPORTED,
@@ -373,6 +389,7 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   p.flags = d->flags;
   p.n_lines = n_lines;
   pl->nj = nj_bucket(p.B4);
+  pl->persistent = (d->flags & MF_PERSISTENT) != 0;
   pl->use_graph = env_int("MF_GRAPH", 1) != 0;
   pl->pdl = env_int("MF_PDL", 1) != 0;
   p.pf_stages = env_int("MF_PF_STAGES", 4);
@@ -497,6 +514,9 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
       {(void**)&p.k1part, (size_t)k1u * K1E * sizeof(float2)},
       {(void**)&p.k3part, (size_t)k3u * K3E * sizeof(float)},
       {(void**)&p.status, P * sizeof(int)},
+      {(void**)&p.q_words,
+       pl->persistent ? (mf::kQueueHead + P + (size_t)n_lines * p.n_ct) * sizeof(int) : 0},
+      {(void**)&p.q_groups, pl->persistent ? (2 * (size_t)n_lines + 1) * sizeof(int) : 0},
   };
   size_t total = 0;
   for (auto& pc : pieces) total = align_up(total, 256) + align_up(pc.bytes, 256);
@@ -516,10 +536,38 @@ mf_status build_plan(const mf_desc* d, const int64_t* line_rows, int n_lines,
   }
   p.lines = lines_d;
   e = cudaMemset(pl->ws, 0, total);
+  if (e == cudaSuccess && pl->persistent) {
+    // work queue: the first item of every group of a pass, S(0) S(1) X(0)
+    // S(2) X(1) ... S(L-1) X(L-2) X(L-1) (solves of line l: Pl items; pixel
+    // CTAs of line l: n_ct n_rb items), then the pass size
+    std::vector<int> g(2 * (size_t)n_lines + 1);
+    long long at = 0;
+    for (int gi = 0; gi < 2 * n_lines; ++gi) {
+      g[gi] = (int)at;
+      const bool last = gi == 2 * n_lines - 1;
+      if (gi == 0 || ((gi & 1) && !last)) at += p.Pl;
+      else at += (long long)p.n_ct * pl->lines[last ? n_lines - 1 : gi / 2 - 1].n_rb;
+    }
+    g[2 * n_lines] = (int)at;
+    if (at > INT32_MAX) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess)
+      e = cudaMemcpy(const_cast<int*>(p.q_groups), g.data(), g.size() * sizeof(int),
+                     cudaMemcpyHostToDevice);
+    pl->q_bytes = (mf::kQueueHead + P + (size_t)n_lines * p.n_ct) * sizeof(int);
+    p.q_wait_ns = (long long)env_int("MF_QUEUE_WAIT_MS", 2000) * 1000000LL;
+    pl->smem_queue = std::max({pl->smem_pixel, pl->smem_sinit, pl->smem_siter});
+  }
   if (e == cudaSuccess)
     e = cudaMallocHost(&pl->lines_pinned, (size_t)n_lines * sizeof(mf::LineInfo));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->lines_copied, cudaEventDisableTiming);
   if (e == cudaSuccess) e = set_attrs(pl);
+  if (e == cudaSuccess && pl->persistent) {
+    // one wave of the work-queue kernel (queried after its shared-memory
+    // attribute is set)
+    const int per_sm = mf::queue_ctas_per_sm(pl->nj, pl->smem_queue);
+    if (per_sm < 1) e = cudaErrorInvalidConfiguration;
+    pl->grid_queue = per_sm * pl->num_sms;
+  }
   if (e != cudaSuccess) {
     cudaFree(pl->ws);
     if (pl->lines_pinned) cudaFreeHost(pl->lines_pinned);
@@ -588,6 +636,13 @@ mf_status run_retrieval(mf_plan_s* pl, const float* cube, const float* k, double
   auto enqueue = [&](cudaStream_t q) {
     pl->tl_kind.clear();
     cudaMemsetAsync(p.status, 0, (size_t)p.P * sizeof(int), q);
+    if (pl->persistent) {
+      // the statistics pass, then everything else in one launch
+      cudaMemsetAsync(p.q_words, 0, pl->q_bytes, q);
+      stats_dispatch(pl, p, mf::STAT_INIT, 0, q);
+      queue_dispatch(pl, p, n_iter_max, q);
+      return;
+    }
     stats_dispatch(pl, p, mf::STAT_INIT, 0, q);
     solve_init_dispatch(pl, p, q);
     pixel_dispatch(pl, p, mf::PIX_INIT, n_iter_max > 0, 0, q);
@@ -1097,6 +1152,15 @@ mf_status mf_plan_status(mf_plan_t pl, int32_t* status) {
   MF_CUDA(cudaStreamSynchronize(pl->last_stream));
   MF_CUDA(cudaMemcpy(status, pl->prm.status, (size_t)pl->prm.P * sizeof(int),
                      cudaMemcpyDeviceToHost));
+  if (pl->persistent) {
+    // a work-queue retrieval that stopped early leaves items undone: every
+    // partition is suspect
+    int abort_word = 0;
+    MF_CUDA(cudaMemcpy(&abort_word, pl->prm.q_words + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (abort_word != 0)
+      for (int i = 0; i < pl->prm.P; ++i)
+        if (status[i] == MF_OK) status[i] = MF_ERR_TIMEOUT;
+  }
   for (int i = 0; i < pl->prm.P; ++i)
     if (status[i] != MF_OK) return (mf_status)status[i];
   return MF_OK;

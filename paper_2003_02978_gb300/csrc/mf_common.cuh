@@ -50,6 +50,9 @@ enum : int { PS_Q = 0, PS_MUV, PS_COFF, PS_INVMU2, PS_N };
 enum : int { DS_N = 0, DS_BBAR, DS_Q, DS_N2 };
 
 enum : int { STAT_INIT = 0, STAT_LITERAL = 1 };
+// Params::q_words: the 64-bit next-item counter, the abort word and a pad
+// before the per-partition words
+constexpr int kQueueHead = 4;
 enum : int { PIX_INIT = 0, PIX_ITER = 1 };
 enum : int { SOLVE_FUSED = 0, SOLVE_MEAN_ONLY = 1 };
 
@@ -137,6 +140,15 @@ struct Params {
   // the solve kernels prefetch into L2 the first pf_stages stages of every
   // pixel CTA of the pass that follows them (0: off; single-line plans)
   int pf_stages;
+  // persistent work queue (MF_PERSISTENT, mf_queue.cu): q_words holds the
+  // next item, the abort flag, per partition the passes whose solve has
+  // completed (P) and per line and column tile the pixel items completed
+  // over all passes (n_lines n_ct), zeroed before every retrieval; q_groups
+  // the first item of each of the 2 n_lines groups of a pass, then the pass
+  // size; q_wait_ns bounds each dependency wait
+  int* q_words;
+  const int* q_groups;
+  long long q_wait_ns;
 };
 
 // Programmatic dependent launch.  A kernel launched with the programmatic
@@ -185,8 +197,8 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 struct LaunchSpan {
   unsigned long long* s;
-  __device__ explicit LaunchSpan(const Params& p)
-      : s(p.tl && threadIdx.x == 0 ? p.tl + 2 * (size_t)p.tl_slot : nullptr) {
+  __device__ explicit LaunchSpan(const Params& p, bool on = true)
+      : s(on && p.tl && threadIdx.x == 0 ? p.tl + 2 * (size_t)p.tl_slot : nullptr) {
     if (s) atomicMax(s, ~globaltimer_ns());
   }
   __device__ ~LaunchSpan() {
@@ -330,6 +342,11 @@ void stats_tc_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtens
 void pilot_launch(cudaStream_t s, const Params& p);
 void pilot_dirs_launch(cudaStream_t s, const Params& p);
 void energy_final_launch(cudaStream_t s, const Params& p, int k);
+// persistent work queue (mf_queue.cu)
+cudaError_t queue_set_attributes(int nj, size_t smem);
+int queue_ctas_per_sm(int nj, size_t smem);
+void queue_launch(int nj, int grid, size_t smem, cudaStream_t s, const CUtensorMap& map,
+                  const Params& p, int n_iter_max);
 // backward pass (mf_backward.cu)
 size_t bwd_pixel_smem_bytes(int B, int nj);
 size_t bwd_solve_smem_bytes(int B);

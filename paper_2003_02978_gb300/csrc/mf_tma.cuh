@@ -68,6 +68,11 @@ __device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, lo
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// generic-proxy writes to global memory (observed through an acquire) ->
+// later async-proxy reads of it (bulk copies)
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 
 // 3-D tiled TMA load of one box into shared memory, completing on `bar`
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,

@@ -1,5 +1,6 @@
 """Autotuner of the launch shapes of a plan (rows per pixel-kernel CTA, rows
-per statistics work item), with a JSON cache.
+per statistics work item) and of its schedule (a launch per pass, or the
+persistent work queue of MF_PERSISTENT), with a JSON cache.
 
 For a shape (columns, bands, line lengths, precision, flags) it times a few
 candidate shapes on the caller's own cube with CUDA events (one warm-up and
@@ -70,10 +71,11 @@ def _time(plan, cube, k, lam, eps, n_iter, mask, reps):
 def autotune(cube, k, lam, eps, n_iter, mask=None, line_rows=None, band_lo=0, band_hi=None,
              col_group=1, flags=3, precision=0, reps=3, use_cache=True, verbose=False,
              candidates=None):
-    """Best {pixel_rows, stat_rows} for this cube's shape (a dict for the
-    ``tuning`` argument of Plan / BatchPlan), timing candidates on the cube.
-    ``candidates``: optional (pixel_rows, stat_rows) pairs to try instead of
-    the full grid PIXEL_ROWS x STAT_ROWS."""
+    """Best {pixel_rows, stat_rows, persistent} for this cube's shape (a dict
+    for the ``tuning`` argument of Plan / BatchPlan), timing candidates on the
+    cube.  ``candidates``: optional (pixel_rows, stat_rows[, persistent])
+    tuples to try instead of the full grid PIXEL_ROWS x STAT_ROWS (launch per
+    pass) plus the default shapes in the persistent schedule."""
     rows, cols, bt = cube.shape
     band_hi = bt if band_hi is None else band_hi
     line_rows = [rows] if line_rows is None else list(line_rows)
@@ -82,11 +84,15 @@ def autotune(cube, k, lam, eps, n_iter, mask=None, line_rows=None, band_lo=0, ba
     if key in cache:
         return dict(cache[key]["tuning"])
     if candidates is None:
-        candidates = [(pr, sr) for pr in PIXEL_ROWS for sr in STAT_ROWS]
-    candidates = [(pr, sr) for pr, sr in candidates if not (precision == 1 and sr > 1024)]
+        candidates = [(pr, sr, 0) for pr in PIXEL_ROWS for sr in STAT_ROWS] + [(0, 0, 1)]
+    candidates = [tuple(c) + (0,) * (3 - len(c)) for c in candidates]
+    # the BF16-split bound is stated up to 1024 rows per statistics item; the
+    # persistent schedule runs the fused iterations only
+    candidates = [(pr, sr, pq) for pr, sr, pq in candidates
+                  if not (precision == 1 and sr > 1024) and not (pq and flags & 4)]
     results = []
-    for pr, sr in candidates:
-        t = {"pixel_rows": pr, "stat_rows": sr}
+    for pr, sr, pq in candidates:
+        t = {"pixel_rows": pr, "stat_rows": sr, "persistent": pq}
         if len(line_rows) == 1:
             plan = Plan(rows, cols, bt, band_lo, band_hi, col_group, flags, precision,
                         tuning=t)
@@ -97,7 +103,7 @@ def autotune(cube, k, lam, eps, n_iter, mask=None, line_rows=None, band_lo=0, ba
         plan.close()
         results.append((ms, t))
         if verbose:
-            print(f"  pixel_rows={pr:5d} stat_rows={sr:5d}: {ms:.3f} ms")
+            print(f"  pixel_rows={pr:5d} stat_rows={sr:5d} persistent={pq}: {ms:.3f} ms")
     ms, best = min(results, key=lambda r: r[0])
     if use_cache:
         cache[key] = {"tuning": best, "ms": ms,

@@ -60,12 +60,16 @@ def test_autotune_picks_a_candidate_and_caches(tmp_path, monkeypatch):
     monkeypatch.setenv("MF_TUNE_CACHE", str(tmp_path / "tune.json"))
     sc, prm = workload_scene("plain-512x16x72", seed=6, device="cuda")
     best = tune.autotune(sc.cube, sc.k, prm["lam"], prm["eps"], prm["n_iter"], reps=1)
-    assert set(best) == {"pixel_rows", "stat_rows"}
+    assert set(best) == {"pixel_rows", "stat_rows", "persistent"}
     assert best["pixel_rows"] in tune.PIXEL_ROWS and best["stat_rows"] in tune.STAT_ROWS
+    assert best["persistent"] in (0, 1)
     cache = json.loads((tmp_path / "tune.json").read_text())
     (entry,) = cache.values()
     assert entry["tuning"] == best
-    assert len(entry["candidates"]) == len(tune.PIXEL_ROWS) * len(tune.STAT_ROWS)
+    # the shape grid in the launch-per-pass schedule, the default shape in the
+    # persistent one
+    assert len(entry["candidates"]) == len(tune.PIXEL_ROWS) * len(tune.STAT_ROWS) + 1
+    assert sum(c["tuning"]["persistent"] for c in entry["candidates"]) == 1
     # cached: returned without timing again
     assert tune.autotune(sc.cube, sc.k, prm["lam"], prm["eps"], prm["n_iter"]) == best
     # the tuned plan computes the same retrieval (within the float32 bar)
