@@ -427,6 +427,31 @@ def precision_form(dev, n_cols=8):
 BATCH_LINES = 64
 
 
+def persistent_only(args, mfg, run, shape, dev, world, stream):
+    """The headline workload (BF16-split statistics, fused iterations) in the
+    persistent work-queue schedule: pilot, statistics, then one queue_kernel
+    launch per retrieval, replayed as a CUDA graph.  Prints one JSON line of
+    its own (not the bench contract's line)."""
+    rows, cols, bands = shape
+    plan = mfg.Plan(rows, cols, bands, flags=mfg.ALBEDO | mfg.SPARSE | mfg.PERSISTENT,
+                    precision=mfg.BF16SPLIT)
+    run(plan)
+    ms = time_retrievals(plan, run, args.steps, args.warmup, dev, world, stream)
+    plan.timeline(True)
+    run(plan)
+    plan.timeline_read()
+    run(plan)
+    spans = plan.timeline_read()
+    plan.timeline(False)
+    ok = bool(np.all(plan.status() == 0))
+    plan.close()
+    print(json.dumps({"workload": WORKLOAD, "schedule": "persistent work queue (MF_PERSISTENT)",
+                      "value": rows * cols / (ms * 1e-3) / 1e6, "unit": "Mpixel/s",
+                      "ms_per_step": ms, "steps": args.steps, "status_ok": ok,
+                      "launches_per_retrieval": [[kd, round(t1 - t0, 1)] for kd, t0, t1 in spans]}),
+          flush=True)
+
+
 def batched_form(dev, precision, n_lines=BATCH_LINES):
     """The batched workload: `n_lines` flightlines (rows uniform in
     2000-30000, 598 x 72, per-column masked fraction U(0, 0.3), per-line
@@ -656,6 +681,9 @@ def main():
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation form")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision form")
     ap.add_argument("--batch-lines", type=int, default=BATCH_LINES)
+    ap.add_argument("--persistent-only", action="store_true",
+                    help="time only the headline workload in the persistent work-queue schedule "
+                         "(MF_PERSISTENT) and print its own line (for profiling that kernel)")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -681,6 +709,10 @@ def main():
 
     def run(plan):
         plan.retrieve(sc.cube, k, prm["lam"], prm["eps"], n_iter, mask=sc.mask, out=out)
+
+    if args.persistent_only:
+        persistent_only(args, mfg, run, sc.cube.shape, dev, world, stream)
+        return
 
     # --- headline form: fused schedule, moments on the tensor cores (bf16
     # hi + lo split, float32 accumulation), float32 pixel path, double-float
