@@ -178,3 +178,25 @@ def test_queue_wait_runs_out_and_context_survives(mfg, monkeypatch):
 def test_queue_rejects_literal(mfg):
     with pytest.raises(mfg.MFError):
         mfg.Plan(512, 16, 72, flags=ALBEDO | SPARSE | PERSISTENT | 4)
+
+
+def test_queue_checkpointed_forward_and_gradients(mfg):
+    """The differentiation form's forward (checkpoints of every pass) through
+    the work queue: alpha and the gradients the adjoint computes from the
+    checkpoint agree bit for bit with the launch-per-pass forward."""
+    sc, prm = workload_scene("plain-512x16x72", seed=7, mask_frac=0.05)
+    cube, mask = sc.cube.cuda(), sc.mask.cuda()
+    rng = np.random.default_rng(0)
+    g = torch.as_tensor(rng.standard_normal((512, 16)), dtype=torch.float32).cuda()
+    res = []
+    for extra in (0, PERSISTENT):
+        plan = mfg.Plan(512, 16, 72, flags=ALBEDO | SPARSE | extra)
+        alpha, ck = plan.retrieve_train(cube, np.asarray(f32(sc.k), np.float32), prm["lam"],
+                                        prm["eps"], 4, mask=mask, cube_grad=True)
+        gk, gl, gc = plan.backward(ck, g, cube_grad=True)
+        torch.cuda.synchronize()
+        res.append([t.detach().cpu().clone() for t in (alpha, gk, gl.reshape(1), gc)])
+        assert np.all(plan.status() == 0)
+        plan.close()
+    for a, b in zip(res[0], res[1]):
+        assert same_bits(a, b)
