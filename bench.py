@@ -487,10 +487,14 @@ def batched_form(dev, precision, n_lines=BATCH_LINES):
     k = torch.as_tensor(k_np, device=dev)
     npix = R * cols
     t0 = time.perf_counter()
+    # shapes for both schedules: the persistent one gains from longer pixel
+    # items (fewer items to take and wait for)
+    tuned = []
     tuning = tune.autotune(cube, k, lams, 1e-9, nits, mask=mask, line_rows=rows,
                            precision=precision, reps=1, use_cache=False,
-                           candidates=[(0, 0), (256, 0), (512, 0), (0, 512), (256, 512),
-                                       (512, 512), (0, 0, 1)])
+                           candidates=[(0, 0, 0), (256, 0, 0), (1024, 0, 0), (0, 512, 0),
+                                       (256, 512, 0), (1024, 512, 0), (0, 0, 1), (1024, 0, 1),
+                                       (2048, 0, 1), (4096, 0, 1)], results_out=tuned)
     tune_s = time.perf_counter() - t0
     plan = mfg.BatchPlan(rows, cols, bands, precision=precision, tuning=tuning)
     out = torch.empty((R, cols), dtype=torch.float32, device=dev)
@@ -502,21 +506,29 @@ def batched_form(dev, precision, n_lines=BATCH_LINES):
     status_ok = bool(np.all(plan.status() == 0))
     slices = plan.line_slices()
     plan.close()
-    # the other schedule with the same shapes: one launch per pass (a CUDA
-    # graph of ~2 n_iter launches) or the persistent work queue (one launch
-    # after the statistics); the same arithmetic, so bit-identical alpha
-    other = dict(tuning, persistent=0 if tuning.get("persistent") else 1)
-    plan_o = mfg.BatchPlan(rows, cols, bands, precision=precision, tuning=other)
+    # the other schedule, one launch per pass (a CUDA graph of ~2 n_iter
+    # launches) or the persistent work queue (one launch after the
+    # statistics): timed at its own best shapes, and run once at the chosen
+    # shapes, where the arithmetic is the same, to check bit-identical alpha
+    other_p = 0 if tuning.get("persistent") else 1
+    other = min((r for r in tuned if r[1]["persistent"] == other_p), key=lambda r: r[0])[1]
     out_o = torch.empty_like(out)
 
     def run_o(pl):
         pl.retrieve(cube, k, lams, 1e-9, nits, mask=mask, out=out_o)
 
+    plan_o = mfg.BatchPlan(rows, cols, bands, precision=precision, tuning=other)
     ms_o = time_retrievals(plan_o, run_o, 3, 2, dev)
-    same_bits = bool(torch.equal(out.view(torch.int32), out_o.view(torch.int32)))
     plan_o.close()
+    plan_s = mfg.BatchPlan(rows, cols, bands, precision=precision,
+                           tuning=dict(tuning, persistent=other_p))
+    run_o(plan_s)
+    torch.cuda.synchronize(dev)
+    same_bits = bool(torch.equal(out.view(torch.int32), out_o.view(torch.int32)))
+    plan_s.close()
     del out_o
     ms_seq, ms_queue = (ms_o, ms_b) if tuning.get("persistent") else (ms_b, ms_o)
+    tuning_seq, tuning_queue = (other, tuning) if tuning.get("persistent") else (tuning, other)
     # plain FP32 form: literal schedule, one plan per line
     outp = torch.empty_like(out)
     ms_p = 0.0
@@ -550,8 +562,10 @@ def batched_form(dev, precision, n_lines=BATCH_LINES):
            "value": npix / (ms_b * 1e-3) / 1e6, "ms_per_batch": ms_b,
            "schedule": "persistent work queue" if tuning.get("persistent") else "launch per pass",
            "launch_per_pass_value": npix / (ms_seq * 1e-3) / 1e6,
+           "launch_per_pass_tuning": tuning_seq,
            "persistent_value": npix / (ms_queue * 1e-3) / 1e6,
-           "schedules_bit_identical": same_bits,
+           "persistent_tuning": tuning_queue,
+           "schedules_bit_identical_at_equal_shapes": same_bits,
            "plain_fp32_value": npix / (ms_p * 1e-3) / 1e6, "plain_fp32_ms": ms_p,
            "status_ok": status_ok}
     return res, {"k": k_np, "samples": samples}

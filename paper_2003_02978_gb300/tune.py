@@ -70,12 +70,13 @@ def _time(plan, cube, k, lam, eps, n_iter, mask, reps):
 
 def autotune(cube, k, lam, eps, n_iter, mask=None, line_rows=None, band_lo=0, band_hi=None,
              col_group=1, flags=3, precision=0, reps=3, use_cache=True, verbose=False,
-             candidates=None):
+             candidates=None, results_out=None):
     """Best {pixel_rows, stat_rows, persistent} for this cube's shape (a dict
     for the ``tuning`` argument of Plan / BatchPlan), timing candidates on the
     cube.  ``candidates``: optional (pixel_rows, stat_rows[, persistent])
     tuples to try instead of the full grid PIXEL_ROWS x STAT_ROWS (launch per
-    pass) plus the default shapes in the persistent schedule."""
+    pass) plus the default shapes in the persistent schedule.  ``results_out``:
+    a list that receives every timed candidate as (ms, tuning)."""
     rows, cols, bt = cube.shape
     band_hi = bt if band_hi is None else band_hi
     line_rows = [rows] if line_rows is None else list(line_rows)
@@ -104,6 +105,8 @@ def autotune(cube, k, lam, eps, n_iter, mask=None, line_rows=None, band_lo=0, ba
         results.append((ms, t))
         if verbose:
             print(f"  pixel_rows={pr:5d} stat_rows={sr:5d} persistent={pq}: {ms:.3f} ms")
+    if results_out is not None:
+        results_out.extend(results)
     ms, best = min(results, key=lambda r: r[0])
     if use_cache:
         cache[key] = {"tuning": best, "ms": ms,
