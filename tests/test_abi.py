@@ -36,6 +36,15 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_flag_values_match_the_binding():
+    import paper_2003_02978_gb300 as mfg
+    src = open(os.path.join(ROOT, "include", "mf.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"#define MF_([A-Z_]+)\s+(\d+)u", src)}
+    for name in ("ALBEDO", "SPARSE", "LITERAL", "PENALTY_NO_ALBEDO", "PERSISTENT"):
+        assert defs[name] == getattr(mfg, name), name
+
+
 def test_status_strings(lib):
     for s in range(0, 9):
         assert lib.mf_status_string(s)
@@ -54,7 +63,8 @@ def _desc(**kw):
     (dict(band_hi=80), 1), (dict(col_group=0), 1), (dict(layout=3), 8),
     (dict(precision=7), 1), (dict(precision=1, bands_total=128, band_hi=128), 8),
     (dict(precision=1, bands_total=32, band_hi=32), 8), (dict(precision=1, band_lo=12), 8),
-    (dict(flags=1 << 9), 1), (dict(band_lo=2, band_hi=74, bands_total=80), 8),
+    (dict(flags=1 << 9), 1), (dict(flags=3 | 4 | 16), 1),  # MF_PERSISTENT with MF_LITERAL
+    (dict(band_lo=2, band_hi=74, bands_total=80), 8),
     (dict(band_lo=0, band_hi=6), 8), (dict(bands_total=200, band_hi=200), 8),
 ])
 def test_descriptor_validation(lib, kw, code):
